@@ -1,0 +1,465 @@
+/*
+ * FP64 CPU oracle for NIPALS-PCA and GS-PCA, written from Andrecut,
+ * "Parallel GPU Implementation of Iterative PCA Algorithms" (arXiv:0811.1081).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no
+ * code, header or constant with the CUDA library it checks, and it never
+ * calls it.
+ *
+ * Conventions
+ *   - Every matrix is column-major with leading dimension = its row count:
+ *     element (m, n) of an M x N matrix lives at [n*M + m] (Sec. 3: "Matrix A
+ *     is stored in column major format").
+ *   - Arithmetic is IEEE-754 double, round to nearest, one rounding per
+ *     operation (build with -ffp-contract=off), every sum in plain index
+ *     order.  No blocking, no reordering, no BLAS.
+ *   - Readings of points the paper leaves open (each one is listed with its
+ *     reason in the design notes of the repository):
+ *       * convergence test: relative and strict, |lambda' - lambda| < tol*lambda',
+ *         lambda starting at 0, at most max_iter iterations (the test used in
+ *         all four appendix programs; Sec. 2.2/2.3 print it as absolute);
+ *       * Gram-Schmidt: one classical pass per half-iteration (Sec. 2.3
+ *         pseudo-code, as in the appendix programs);
+ *       * zero start column: when column k of the residual is exactly zero,
+ *         start from the residual column of largest norm (lowest index on
+ *         ties); when every column is zero the fit stops as degenerate;
+ *       * rank exhausted: a norm <= 64*eps64*||X||_F stops the fit as
+ *         degenerate; the components found so far are kept, the rest are 0;
+ *       * NIPALS returns lambda_k = ||t_k|| (the pseudo-code's lambda').
+ *   - Status codes: 0 ok, 1 invalid argument, 4 at least one component hit
+ *     max_iter, 5 degenerate (fewer than K components found).
+ *
+ * Parity pins for every function here live in tests/test_oracle_pins.py.
+ */
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_INVALID 1
+#define OR_NOT_CONVERGED 4
+#define OR_DEGENERATE 5
+
+/* ---------------------------------------------------------------- helpers */
+
+static double dot(const double *x, const double *y, int n)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; i++)
+        s += x[i] * y[i];
+    return s;
+}
+
+/* Euclidean norm, Sec. 3 (nrm2): square root of the sum of squares. */
+static double nrm2(const double *x, int n)
+{
+    return sqrt(dot(x, x, n));
+}
+
+static void scal(double *x, int n, double alpha)
+{
+    for (int i = 0; i < n; i++)
+        x[i] *= alpha;
+}
+
+/* y = A^T x for A (rows x cols), i.e. y[c] = sum_r A[r,c] x[r]  (gemv 't'). */
+static void gemv_t(const double *A, int rows, int cols, const double *x, double *y)
+{
+    for (int c = 0; c < cols; c++)
+        y[c] = dot(A + (size_t)c * rows, x, rows);
+}
+
+/* y = A x for A (rows x cols), i.e. y[r] = sum_c A[r,c] x[c]  (gemv 'n').
+ * The sum over c for each row is taken in index order c = 0, 1, ... */
+static void gemv_n(const double *A, int rows, int cols, const double *x, double *y)
+{
+    for (int r = 0; r < rows; r++) {
+        double s = 0.0;
+        for (int c = 0; c < cols; c++)
+            s += A[(size_t)c * rows + r] * x[c];
+        y[r] = s;
+    }
+}
+
+/* A <- A + alpha x y^T  (ger, Eq. 3 deflation). */
+static void ger(double *A, int rows, int cols, double alpha, const double *x, const double *y)
+{
+    for (int c = 0; c < cols; c++) {
+        double ay = alpha * y[c];
+        double *col = A + (size_t)c * rows;
+        for (int r = 0; r < rows; r++)
+            col[r] += x[r] * ay;
+    }
+}
+
+/* One classical Gram-Schmidt pass of x against the first k columns of Q
+ * (Sec. 2.3): coef = Q_(k)^T x, then x <- x - Q_(k) coef.  All k coefficients
+ * are taken from the unmodified x (classical, not modified, Gram-Schmidt). */
+static void cgs_pass(const double *Q, int rows, int k, double *x, double *coef)
+{
+    gemv_t(Q, rows, k, x, coef);
+    for (int j = 0; j < k; j++) {
+        const double *q = Q + (size_t)j * rows;
+        for (int r = 0; r < rows; r++)
+            x[r] -= q[r] * coef[j];
+    }
+}
+
+static double frob(const double *A, int rows, int cols)
+{
+    return nrm2(A, rows * cols);
+}
+
+/* Start column for component k: column k of the residual, unless it is
+ * exactly zero; then the column of largest norm (lowest index on ties).
+ * Returns -1 when every column is zero. */
+static int start_column(const double *R, int M, int N, int k)
+{
+    if (nrm2(R + (size_t)k * M, M) != 0.0)
+        return k;
+    int best = -1;
+    double bestn = 0.0;
+    for (int c = 0; c < N; c++) {
+        double n = nrm2(R + (size_t)c * M, M);
+        if (n > bestn) {
+            bestn = n;
+            best = c;
+        }
+    }
+    return best;
+}
+
+/* Convergence bookkeeping shared by both algorithms.  j is the number of
+ * completed iterations.  Returns 1 when the loop must stop. */
+static int stop_now(int j, double prev, double cur, double tol, int max_iter,
+                    const int *iters_lock, int k, int *not_converged)
+{
+    if (iters_lock)
+        return j >= iters_lock[k];
+    if (fabs(prev - cur) < tol * cur)
+        return 1;
+    if (j >= max_iter) {
+        *not_converged = 1;
+        return 1;
+    }
+    return 0;
+}
+
+static void zero_tail(double *T, double *P, double *lambda, int *iters,
+                      int M, int N, int K, int k)
+{
+    for (int j = k; j < K; j++) {
+        memset(T + (size_t)j * M, 0, sizeof(double) * M);
+        memset(P + (size_t)j * N, 0, sizeof(double) * N);
+        lambda[j] = 0.0;
+        iters[j] = 0;
+    }
+}
+
+/* ------------------------------------------------------------- centring */
+
+/* mode 1: every column loses its own mean (the prose of Sec. 2.1: "each
+ *         column is mean centered").
+ * mode 2: Eq. 1 as printed: the average column N^-1 sum_n X^(n) is
+ *         subtracted from every column, so each row ends with zero mean. */
+int oracle_center(double *R, int M, int N, int mode)
+{
+    if (M < 1 || N < 1)
+        return OR_INVALID;
+    if (mode == 0)
+        return OR_OK;
+    if (mode == 1) {
+        for (int c = 0; c < N; c++) {
+            double *col = R + (size_t)c * M;
+            double s = 0.0;
+            for (int r = 0; r < M; r++)
+                s += col[r];
+            double mean = s / M;
+            for (int r = 0; r < M; r++)
+                col[r] -= mean;
+        }
+        return OR_OK;
+    }
+    if (mode == 2) {
+        double *avg = calloc((size_t)M, sizeof(double));
+        if (!avg)
+            return OR_INVALID;
+        for (int c = 0; c < N; c++)
+            for (int r = 0; r < M; r++)
+                avg[r] += R[(size_t)c * M + r];
+        for (int r = 0; r < M; r++)
+            avg[r] /= N;
+        for (int c = 0; c < N; c++)
+            for (int r = 0; r < M; r++)
+                R[(size_t)c * M + r] -= avg[r];
+        free(avg);
+        return OR_OK;
+    }
+    return OR_INVALID;
+}
+
+/* --------------------------------------------------------------- NIPALS */
+
+/* NIPALS-PCA, Sec. 2.2 pseudo-code:
+ *   R <- X
+ *   for k: lambda = 0; T(k) <- R(k)
+ *     repeat: P(k) <- R^T T(k); P(k) <- P(k)/||P(k)||; T(k) <- R P(k);
+ *             lambda' <- ||T(k)||; stop when converged; lambda <- lambda'
+ *     R <- R - T(k) P(k)^T            (Eq. 3)
+ * T keeps the unnormalised scores, so X = T P^T + R (Eq. 4). */
+static int nipals(double *R, int M, int N, int K, double tol, int max_iter,
+                  const int *iters_lock, double thresh,
+                  double *T, double *P, double *lambda, int *iters, int *found)
+{
+    int not_converged = 0;
+    for (int k = 0; k < K; k++) {
+        double *t = T + (size_t)k * M;
+        double *p = P + (size_t)k * N;
+        int c = start_column(R, M, N, k);
+        if (c < 0) {
+            *found = k;
+            zero_tail(T, P, lambda, iters, M, N, K, k);
+            return OR_DEGENERATE;
+        }
+        memcpy(t, R + (size_t)c * M, sizeof(double) * M);
+        double prev = 0.0, cur = 0.0;
+        int j = 0;
+        for (;;) {
+            gemv_t(R, M, N, t, p);
+            double np = nrm2(p, N);
+            if (np == 0.0) {
+                *found = k;
+                zero_tail(T, P, lambda, iters, M, N, K, k);
+                return OR_DEGENERATE;
+            }
+            scal(p, N, 1.0 / np);
+            gemv_n(R, M, N, p, t);
+            cur = nrm2(t, M);
+            if (cur <= thresh) {
+                *found = k;
+                zero_tail(T, P, lambda, iters, M, N, K, k);
+                return OR_DEGENERATE;
+            }
+            j++;
+            if (stop_now(j, prev, cur, tol, max_iter, iters_lock, k, &not_converged))
+                break;
+            prev = cur;
+        }
+        lambda[k] = cur;
+        iters[k] = j;
+        ger(R, M, N, -1.0, t, p);
+    }
+    *found = K;
+    return not_converged ? OR_NOT_CONVERGED : OR_OK;
+}
+
+/* ------------------------------------------------------------------ GS-PCA */
+
+/* GS-PCA, Sec. 2.3 pseudo-code (truncated-SVD form, Eq. 5):
+ *   R <- X
+ *   for k: mu = 0; V(k) <- R(k)
+ *     repeat: U(k) <- R^T V(k)
+ *             if k>0: A <- U_(k)^T U(k); U(k) <- U(k) - U_(k) A
+ *             U(k) <- U(k)/||U(k)||
+ *             V(k) <- R U(k)
+ *             if k>0: B <- V_(k)^T V(k); V(k) <- V(k) - V_(k) B
+ *             lambda_k <- ||V(k)||; V(k) <- V(k)/lambda_k
+ *             stop when converged; mu <- lambda_k
+ *     R <- R - lambda_k V(k) U(k)^T
+ *   T <- V Lambda; P <- U
+ * While a component is being extracted, column j < k of T holds V(j) (unit
+ * norm); the scaling T = V Lambda happens once at the end. */
+static int gspca(double *R, int M, int N, int K, double tol, int max_iter,
+                 const int *iters_lock, double thresh,
+                 double *T, double *P, double *lambda, int *iters, int *found)
+{
+    int not_converged = 0, status = OR_OK, kfound = K;
+    double *coef = malloc(sizeof(double) * (size_t)(K > 0 ? K : 1));
+    if (!coef)
+        return OR_INVALID;
+    for (int k = 0; k < K; k++) {
+        double *v = T + (size_t)k * M;
+        double *u = P + (size_t)k * N;
+        int c = start_column(R, M, N, k);
+        if (c < 0) {
+            kfound = k;
+            status = OR_DEGENERATE;
+            break;
+        }
+        memcpy(v, R + (size_t)c * M, sizeof(double) * M);
+        double mu = 0.0, lam = 0.0;
+        int j = 0, degenerate = 0;
+        for (;;) {
+            gemv_t(R, M, N, v, u);
+            if (k > 0)
+                cgs_pass(P, N, k, u, coef);
+            double nu = nrm2(u, N);
+            if (nu == 0.0) {
+                degenerate = 1;
+                break;
+            }
+            scal(u, N, 1.0 / nu);
+            gemv_n(R, M, N, u, v);
+            if (k > 0)
+                cgs_pass(T, M, k, v, coef);
+            lam = nrm2(v, M);
+            if (lam <= thresh) {
+                degenerate = 1;
+                break;
+            }
+            scal(v, M, 1.0 / lam);
+            j++;
+            if (stop_now(j, mu, lam, tol, max_iter, iters_lock, k, &not_converged))
+                break;
+            mu = lam;
+        }
+        if (degenerate) {
+            kfound = k;
+            status = OR_DEGENERATE;
+            break;
+        }
+        lambda[k] = lam;
+        iters[k] = j;
+        ger(R, M, N, -lam, v, u);
+    }
+    free(coef);
+    for (int k = 0; k < kfound; k++)
+        scal(T + (size_t)k * M, M, lambda[k]);
+    if (kfound < K)
+        zero_tail(T, P, lambda, iters, M, N, K, kfound);
+    *found = kfound;
+    if (status == OR_OK && not_converged)
+        status = OR_NOT_CONVERGED;
+    return status;
+}
+
+/* ------------------------------------------------------------ entry point */
+
+/* algo 0 = NIPALS-PCA, 1 = GS-PCA.  X (M x N) is read only; R receives the
+ * final residual (X, centred as requested, minus every extracted component).
+ * iters_lock (nullable): run exactly iters_lock[k] iterations for component k
+ * and ignore the convergence test (used to replay another implementation's
+ * iteration counts).  Outputs: T (M x K), P (N x K), lambda (K), iters (K),
+ * found (number of components extracted). */
+int oracle_fit(int algo, const double *X, int M, int N, int K, double tol, int max_iter,
+               int center, const int *iters_lock,
+               double *T, double *P, double *lambda, int *iters, double *R, int *found)
+{
+    if (!X || !T || !P || !lambda || !iters || !R || !found)
+        return OR_INVALID;
+    if (M < 1 || N < 1 || K < 1 || K > M || K > N || !(tol > 0.0) || max_iter < 1)
+        return OR_INVALID;
+    if (algo != 0 && algo != 1)
+        return OR_INVALID;
+    if (iters_lock)
+        for (int k = 0; k < K; k++)
+            if (iters_lock[k] < 1)
+                return OR_INVALID;
+    memcpy(R, X, sizeof(double) * (size_t)M * N);
+    int st = oracle_center(R, M, N, center);
+    if (st != OR_OK)
+        return st;
+    double thresh = 64.0 * DBL_EPSILON * frob(R, M, N);
+    if (algo == 0)
+        return nipals(R, M, N, K, tol, max_iter, iters_lock, thresh, T, P, lambda, iters, found);
+    return gspca(R, M, N, K, tol, max_iter, iters_lock, thresh, T, P, lambda, iters, found);
+}
+
+/* ------------------------------------------------------- Jacobi eigensolver */
+
+/* Cyclic-by-row Jacobi method for a symmetric n x n matrix A (Golub & Van
+ * Loan, "Matrix Computations", Sec. 8.5): sweep over every pair (p, q),
+ * p < q, and zero A[p,q] with the rotation J = [[c, s], [-s, c]] that solves
+ * the 2 x 2 symmetric Schur problem, A <- J^T A J, W <- W J; stop when the
+ * off-diagonal Frobenius norm is at most tol * ||A||_F.  A is overwritten;
+ * evals/evecs return the eigenpairs sorted by decreasing eigenvalue
+ * (evecs column-major, n x n).  Returns the number of sweeps, -1 on bad
+ * arguments, -2 when max_sweeps was reached. */
+int oracle_jacobi_eigh(double *A, int n, double tol, int max_sweeps, double *evals, double *evecs)
+{
+    if (!A || !evals || !evecs || n < 1 || max_sweeps < 1)
+        return -1;
+    double *W = calloc((size_t)n * n, sizeof(double));
+    if (!W)
+        return -1;
+    for (int i = 0; i < n; i++)
+        W[(size_t)i * n + i] = 1.0;
+    double anorm = frob(A, n, n);
+    int sweep = 0, done = 0;
+    while (sweep < max_sweeps) {
+        double off = 0.0;
+        for (int q = 0; q < n; q++)
+            for (int p = 0; p < n; p++)
+                if (p != q)
+                    off += A[(size_t)q * n + p] * A[(size_t)q * n + p];
+        if (sqrt(off) <= tol * anorm) {
+            done = 1;
+            break;
+        }
+        sweep++;
+        for (int p = 0; p < n - 1; p++) {
+            for (int q = p + 1; q < n; q++) {
+                double apq = A[(size_t)q * n + p];
+                if (apq == 0.0)
+                    continue;
+                double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                double tau = (aqq - app) / (2.0 * apq);
+                double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                double c = 1.0 / sqrt(1.0 + t * t);
+                double s = t * c;
+                /* A <- A J (columns p and q) */
+                for (int i = 0; i < n; i++) {
+                    double aip = A[(size_t)p * n + i], aiq = A[(size_t)q * n + i];
+                    A[(size_t)p * n + i] = c * aip - s * aiq;
+                    A[(size_t)q * n + i] = s * aip + c * aiq;
+                }
+                /* A <- J^T A (rows p and q) */
+                for (int i = 0; i < n; i++) {
+                    double api = A[(size_t)i * n + p], aqi = A[(size_t)i * n + q];
+                    A[(size_t)i * n + p] = c * api - s * aqi;
+                    A[(size_t)i * n + q] = s * api + c * aqi;
+                }
+                /* W <- W J */
+                for (int i = 0; i < n; i++) {
+                    double wip = W[(size_t)p * n + i], wiq = W[(size_t)q * n + i];
+                    W[(size_t)p * n + i] = c * wip - s * wiq;
+                    W[(size_t)q * n + i] = s * wip + c * wiq;
+                }
+            }
+        }
+    }
+    if (!done) {
+        double off = 0.0;
+        for (int q = 0; q < n; q++)
+            for (int p = 0; p < n; p++)
+                if (p != q)
+                    off += A[(size_t)q * n + p] * A[(size_t)q * n + p];
+        done = sqrt(off) <= tol * anorm;
+    }
+    /* selection sort by decreasing eigenvalue */
+    int *order = malloc(sizeof(int) * (size_t)n);
+    if (!order) {
+        free(W);
+        return -1;
+    }
+    for (int i = 0; i < n; i++)
+        order[i] = i;
+    for (int i = 0; i < n; i++) {
+        int best = i;
+        for (int j = i + 1; j < n; j++)
+            if (A[(size_t)order[j] * n + order[j]] > A[(size_t)order[best] * n + order[best]])
+                best = j;
+        int tmp = order[i];
+        order[i] = order[best];
+        order[best] = tmp;
+    }
+    for (int i = 0; i < n; i++) {
+        evals[i] = A[(size_t)order[i] * n + order[i]];
+        memcpy(evecs + (size_t)i * n, W + (size_t)order[i] * n, sizeof(double) * n);
+    }
+    free(order);
+    free(W);
+    return done ? sweep : -2;
+}
