@@ -1,0 +1,306 @@
+#!/usr/bin/env python3
+"""Benchmark: GS-PCA components/s (and HBM GB/s of the persistent kernel) on
+the 10000 x 2000 planted-spectrum workload, K = 50, tol = 1e-6, FP32.
+
+One step = one complete fit (all K components) through the C ABI with X
+already resident in device memory.  L2 is flushed (a 512 MB device write)
+before every timed step, outside the timed interval.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--algo gs|nipals]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the first components of the fit).
+Under torchrun (N > 1) every rank fits its own replica of the workload; the
+value is the sum over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "GS-PCA components/s (10000x2000 planted spectrum, K=50, tol 1e-6, FP32)"
+UNIT = "components/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        return rank, world, local, dist
+    return 0, 1, 0, None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value, device):
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(X64, w, algo, n_comp):
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    f = oracle.fit(X64, n_comp, tol=w.tol, max_iter=w.max_iter, algo=algo)
+    dt = time.perf_counter() - t0
+    return dt, f
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step fits the first components on the host."""
+    rank, world, local, dist = 0, 1, 0, None
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        if int(os.environ.get("RANK", "0")) != 0:
+            return 0
+    w = synth.WORKLOADS[args.workload]
+    X64 = w.make().astype(np.float32).astype(np.float64)
+    n_comp = args.ref_components
+    for _ in range(args.warmup):
+        cpu_oracle_sample(X64, w, args.algo, n_comp)
+    times = []
+    for _ in range(args.steps):
+        dt, _ = cpu_oracle_sample(X64, w, args.algo, n_comp)
+        times.append(dt)
+    total = sum(times)
+    value = n_comp * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config(w, args, l2="host run"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"first {n_comp} of {w.K} components of {w.name} per step, "
+                                   f"FP64 plain C, 1 thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def config(w, args, l2):
+    return {"workload": w.name, "M": w.M, "N": w.N, "K": w.K, "algo": args.algo, "tol": w.tol,
+            "max_iter": w.max_iter, "storage": "f32", "l2": l2, "parallelism": "replicas"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="planted_10000x2000")
+    ap.add_argument("--algo", default="gs", choices=["gs", "nipals"])
+    ap.add_argument("--ref-components", type=int, default=2)
+    ap.add_argument("--cpu-components", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import paper_0811_1081_gb300 as gp
+
+    gp.load()
+    rank, world, local, dist = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = synth.WORKLOADS[args.workload]
+    X32 = w.make().astype(np.float32)
+    M, N, K = X32.shape[0], X32.shape[1], w.K
+    Xd = torch.from_numpy(X32).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    h = gp.Handle(M, N, K, device=local)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        h.fit(Xd, K, tol=w.tol, max_iter=w.max_iter, algo=args.algo)
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kern_ms, alg_bytes, launches, iters_tot = [], [], 0, []
+    barrier(dist)
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        r = h.fit(Xd, K, tol=w.tol, max_iter=w.max_iter, algo=args.algo)
+        ev[i][1].record(stream)
+        kern_ms.append(r.info["kernel_ms"])
+        alg_bytes.append(r.info["alg_bytes"])
+        launches += r.info["kernel_launches"]
+        iters_tot.append(r.info["total_iters"])
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t_wall
+    barrier(dist)
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = max_over_ranks(dist, sum(step_ms) / 1e3, dev)
+    value = world * K * args.steps / total_s
+    status = r.status
+
+    # roofline of the persistent kernel: algorithmic bytes / its event-timed duration
+    peak, peak_src = measured_peaks()
+    k_s = sum(kern_ms) / 1e3
+    achieved = sum(alg_bytes) / k_s / 1e9
+    kernel_share = sum(kern_ms) / sum(step_ms)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    Xh = torch.from_numpy(X32).pin_memory()
+    outs = {"T": torch.empty((K, M), dtype=torch.float32).pin_memory().numpy(),
+            "P": torch.empty((K, N), dtype=torch.float32).pin_memory().numpy(),
+            "lam": torch.empty(K, dtype=torch.float64).pin_memory().numpy(),
+            "iters": torch.empty(K, dtype=torch.int32).pin_memory().numpy(), "R": None}
+    h.fit_host(Xh, K, tol=w.tol, max_iter=w.max_iter, algo=args.algo, out=outs)
+    e2e_ms = []
+    e2e_steps = max(3, min(args.steps, 5))
+    for i in range(e2e_steps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.fit_host(Xh, K, tol=w.tol, max_iter=w.max_iter, algo=args.algo, out=outs)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_s = max_over_ranks(dist, sum(e2e_ms) / 1e3, dev)
+    e2e_value = world * K * e2e_steps / e2e_s
+    h2d = M * N * 4
+    d2h = (M + N) * K * 4 + K * 8 + K * 4
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config(w, args, l2="flushed before every step (512 MB device write, outside the timed interval)"),
+        "status": gp.status_string(status),
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "fit_kernel<4>",
+                     "peak_source": peak_src, "kernel_share_of_step": kernel_share,
+                     "kernel_ms_mean": statistics.mean(kern_ms),
+                     "alg_bytes_per_launch": statistics.mean(alg_bytes)},
+        "iters_total_per_fit": iters_tot[-1],
+        "wall_s_timed": wall,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": statistics.mean(e2e_ms)},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        X64 = X32.astype(np.float64)
+        dt, f = cpu_oracle_sample(X64, w, args.algo, args.cpu_components)
+        line["cpu_baseline"] = {"value": args.cpu_components / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {args.cpu_components} of {w.K} components of {w.name}, "
+                                          f"FP64 plain C oracle, 1 thread, {dt:.1f} s"}
+    h.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,165 @@
+/*
+ * gspca.h -- C ABI of the GB300 (sm_103a) implementation of the iterative PCA
+ * algorithms of M. Andrecut, "Parallel GPU Implementation of Iterative PCA
+ * Algorithms" (arXiv:0811.1081): NIPALS-PCA (Sec. 2.2) and GS-PCA (Sec. 2.3).
+ *
+ * Problem statement (Sec. 2.1, Eq. 2-5): X is M x N, columns are attributes,
+ * rows are observations.  K components are extracted one at a time by power
+ * iteration on the residual R (R <- X first), each followed by the rank-1
+ * deflation R <- R - T(k) P(k)^T (Eq. 3), so that X = T_(K) P_(K)^T + R
+ * (Eq. 4).  GS-PCA re-orthogonalises the loading against P_(k) and the score
+ * direction against the normalised earlier scores at every iteration with one
+ * classical Gram-Schmidt pass, and returns T = V Lambda, P = U (Eq. 5).
+ *
+ * Conventions shared by every entry point
+ *   - All pointers are plain pointers.  Unless an entry point says "host",
+ *     data pointers are device pointers on the handle's device, and the
+ *     caller owns them.  The library never frees caller memory.
+ *   - X is FP32.  It is read only.  layout = GSPCA_COL_MAJOR means element
+ *     (m, n) at X[n*ldx + m] (ldx >= M; the paper's storage, Sec. 3);
+ *     GSPCA_ROW_MAJOR means X[m*ldx + n] (ldx >= N).
+ *   - Outputs are column-major with leading dimension = rows:
+ *     T is M x K (T[k*M + m]), P is N x K (P[k*N + n]), lambda holds K
+ *     doubles, iters K ints, R_out (optional) is M x N (R_out[n*M + m]).
+ *     GS-PCA: T = V Lambda and lambda_k = ||V(k)|| before normalisation
+ *     (a singular value of the residual).  NIPALS-PCA: T holds the
+ *     unnormalised scores t_k and lambda_k = ||t_k|| (Sec. 2.2).
+ *   - The convergence test is relative and strict: stop when
+ *     |lambda_j - lambda_{j-1}| < tol * lambda_j (lambda_{-1} = 0), or after
+ *     max_iter iterations (the test of the paper's appendix programs).
+ *   - Components past the last one found (status GSPCA_ERR_DEGENERATE) are
+ *     zero in T, P, lambda and iters.
+ *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *     All device work of a call is enqueued on it.  A handle must not be used
+ *     by two calls at once (its workspace is shared by its calls).
+ *   - Errors are reported only through the return value; nothing is printed.
+ */
+#ifndef GSPCA_H
+#define GSPCA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gspca_handle *gspca_t;
+
+typedef enum { GSPCA_NIPALS = 0, GSPCA_GS = 1 } gspca_algo;
+
+/* Storage type of the residual R inside the library (X is always FP32).
+ * GSPCA_BF16: X is rounded to bfloat16 once; every product uses FP32
+ * accumulation and the Gram-Schmidt coefficients, norms and the test stay in
+ * FP64-combined FP32 sums. */
+typedef enum { GSPCA_F32 = 0, GSPCA_BF16 = 1 } gspca_dtype;
+
+typedef enum { GSPCA_COL_MAJOR = 0, GSPCA_ROW_MAJOR = 1 } gspca_layout;
+
+/* Optional centring before the fit (Sec. 2.1, Eq. 1).
+ *   GSPCA_CENTER_COLUMNS: every column loses its own mean (the prose of
+ *                         Sec. 2.1, standard PCA).
+ *   GSPCA_CENTER_ROWS:    Eq. 1 as printed: the average column is subtracted
+ *                         from every column (each row ends with zero mean). */
+typedef enum { GSPCA_CENTER_NONE = 0, GSPCA_CENTER_COLUMNS = 1, GSPCA_CENTER_ROWS = 2 } gspca_center;
+
+typedef enum {
+    GSPCA_OK = 0,
+    GSPCA_ERR_INVALID_ARG = 1,      /* bad size, pointer, tolerance, ... ; nothing was launched */
+    GSPCA_ERR_CUDA = 2,             /* a CUDA call failed; see gspca_last_cuda_error */
+    GSPCA_ERR_OOM = 3,              /* workspace allocation failed */
+    GSPCA_WARN_NOT_CONVERGED = 4,   /* results valid; >= 1 component stopped at max_iter */
+    GSPCA_ERR_DEGENERATE = 5,       /* rank exhausted: fewer than K components found */
+    GSPCA_ERR_TIMEOUT = 6,          /* a bounded device wait gave up; results invalid */
+    GSPCA_ERR_NOT_SUPPORTED = 7     /* sizes beyond what this build handles */
+} gspca_status;
+
+typedef struct {
+    int center;             /* gspca_center, default GSPCA_CENTER_NONE */
+    const int *iters_lock;  /* host array of K counts, nullable: run exactly iters_lock[k]
+                               iterations for component k and ignore the test */
+    int grid_ctas;          /* CTAs of the persistent kernel; 0 = automatic */
+    double timeout_s;       /* limit of every device-side wait; 0 = 2 seconds */
+} gspca_opts;
+
+/* Per-call record of the last fit on a handle (host memory). */
+typedef struct {
+    int found;              /* components extracted */
+    long long total_iters;  /* sum of iters over the components */
+    int kernel_launches;    /* kernels this call enqueued */
+    int grid_ctas;          /* CTAs of the persistent kernel */
+    int block_threads;
+    double alg_bytes;       /* algorithmic bytes of the persistent kernel (one read of R per
+                               pass, deflation write, Gram-Schmidt factor reads) */
+    double kernel_ms;       /* device time of the persistent kernel, from CUDA events recorded
+                               around its launch on the caller's stream */
+} gspca_info;
+
+/* Create a handle on `device` with workspace for problems up to
+ * max_M x max_N and max_K components stored as `dtype`.  The handle owns that
+ * workspace (device memory, freed by gspca_destroy).
+ * Errors: GSPCA_ERR_INVALID_ARG (h NULL, sizes < 1), GSPCA_ERR_NOT_SUPPORTED
+ * (max_N above the per-CTA column limit of this build, 8192), GSPCA_ERR_OOM,
+ * GSPCA_ERR_CUDA. */
+gspca_status gspca_create(gspca_t *h, int device, long max_M, long max_N, int max_K,
+                          gspca_dtype dtype);
+
+/* Fit K components of X (device pointers, see the conventions above).
+ * Sec. 2.2 / 2.3 pseudo-code with a device-resident loop: one persistent
+ * kernel runs every iteration and every convergence decision; the host only
+ * enqueues it and, at the end, synchronises `stream` and reads the status.
+ * Requirements: 1 <= K <= min(M, N), M <= max_M, N <= max_N, K <= max_K,
+ * tol > 0, max_iter >= 1, T, P, lambda non-NULL; iters, R_out, opts nullable.
+ * Returns GSPCA_OK, GSPCA_WARN_NOT_CONVERGED or GSPCA_ERR_DEGENERATE with valid
+ * outputs; other codes leave the outputs unspecified. */
+gspca_status gspca_fit(gspca_t h, void *stream, const float *X, gspca_layout layout, long ldx,
+                       int M, int N, int K, double tol, int max_iter, gspca_algo algo,
+                       float *T, float *P, double *lambda, int *iters, float *R_out,
+                       const gspca_opts *opts);
+
+/* Same as gspca_fit with HOST pointers for X, T, P, lambda, iters and R_out:
+ * the call copies X to the handle's device staging buffer, fits, and copies
+ * the results back, all on `stream`, and returns once they are in host
+ * memory.  The staging buffers are allocated on the first call and owned by
+ * the handle. */
+gspca_status gspca_fit_host(gspca_t h, void *stream, const float *X, gspca_layout layout,
+                            long ldx, int M, int N, int K, double tol, int max_iter,
+                            gspca_algo algo, float *T, float *P, double *lambda, int *iters,
+                            float *R_out, const gspca_opts *opts);
+
+/* One independent problem of a batch (device pointers, same conventions as
+ * gspca_fit, column-major X with leading dimension ldx). */
+typedef struct {
+    const float *X;
+    long ldx;
+    int M, N, K;
+    float *T, *P;
+    double *lambda;
+    int *iters;             /* nullable */
+    int *status;            /* nullable: per-problem gspca_status (device int) */
+} gspca_problem;
+
+/* Fit `count` independent problems (problems[] is a HOST array of
+ * descriptors) with one algorithm, tolerance and iteration cap.  The batch
+ * runs as one persistent launch that takes problems from a device work
+ * queue, largest first.  Returns the worst per-problem status. */
+gspca_status gspca_fit_batched(gspca_t h, void *stream, const gspca_problem *problems, int count,
+                               double tol, int max_iter, gspca_algo algo, const gspca_opts *opts);
+
+/* Record of the last call on h. */
+gspca_status gspca_get_info(gspca_t h, gspca_info *info);
+
+/* Release the handle and its workspace.  NULL is accepted. */
+gspca_status gspca_destroy(gspca_t h);
+
+/* Static English description of a status code (never NULL). */
+const char *gspca_status_string(gspca_status s);
+
+/* Text of the last CUDA error seen by the library in this process (static
+ * storage, never NULL). */
+const char *gspca_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSPCA_H */

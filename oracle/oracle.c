@@ -72,14 +72,17 @@ static void gemv_t(const double *A, int rows, int cols, const double *x, double 
 }
 
 /* y = A x for A (rows x cols), i.e. y[r] = sum_c A[r,c] x[c]  (gemv 'n').
- * The sum over c for each row is taken in index order c = 0, 1, ... */
+ * Every y[r] receives its terms in index order c = 0, 1, ...; the loop runs
+ * over columns so that the column-major matrix is read contiguously. */
 static void gemv_n(const double *A, int rows, int cols, const double *x, double *y)
 {
-    for (int r = 0; r < rows; r++) {
-        double s = 0.0;
-        for (int c = 0; c < cols; c++)
-            s += A[(size_t)c * rows + r] * x[c];
-        y[r] = s;
+    for (int r = 0; r < rows; r++)
+        y[r] = 0.0;
+    for (int c = 0; c < cols; c++) {
+        const double *col = A + (size_t)c * rows;
+        const double xc = x[c];
+        for (int r = 0; r < rows; r++)
+            y[r] += col[r] * xc;
     }
 }
 

@@ -1,0 +1,323 @@
+"""Python binding of the C ABI in ``include/gspca.h``.
+
+Argument marshalling only: every step of NIPALS-PCA / GS-PCA runs in the
+CUDA library ``_lib/libgspca.so`` (built by ``build.py``).  PyTorch supplies
+device memory and the current CUDA stream.  There is no CPU fallback: when
+the library is missing, importing the entry points raises.
+
+Thin wrappers keep the C names (``gspca_create``, ``gspca_fit``,
+``gspca_fit_host``, ``gspca_fit_batched``, ``gspca_get_info``,
+``gspca_destroy``, ``gspca_status_string``); ``Handle`` bundles them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from .buildlib import LIB, build
+
+GSPCA_NIPALS, GSPCA_GS = 0, 1
+GSPCA_F32, GSPCA_BF16 = 0, 1
+GSPCA_COL_MAJOR, GSPCA_ROW_MAJOR = 0, 1
+GSPCA_CENTER_NONE, GSPCA_CENTER_COLUMNS, GSPCA_CENTER_ROWS = 0, 1, 2
+GSPCA_OK = 0
+GSPCA_ERR_INVALID_ARG = 1
+GSPCA_ERR_CUDA = 2
+GSPCA_ERR_OOM = 3
+GSPCA_WARN_NOT_CONVERGED = 4
+GSPCA_ERR_DEGENERATE = 5
+GSPCA_ERR_TIMEOUT = 6
+GSPCA_ERR_NOT_SUPPORTED = 7
+
+EXPORTS = ["gspca_create", "gspca_fit", "gspca_fit_host", "gspca_fit_batched", "gspca_get_info",
+           "gspca_destroy", "gspca_status_string", "gspca_last_cuda_error"]
+
+_ALGOS = {"nipals": GSPCA_NIPALS, "gs": GSPCA_GS, GSPCA_NIPALS: GSPCA_NIPALS, GSPCA_GS: GSPCA_GS}
+_DTYPES = {"f32": GSPCA_F32, "bf16": GSPCA_BF16, GSPCA_F32: GSPCA_F32, GSPCA_BF16: GSPCA_BF16}
+
+
+class GspcaError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = f"{where}: {status_string(status)}"
+        if status == GSPCA_ERR_CUDA:
+            msg += f" ({last_cuda_error()})"
+        super().__init__(msg)
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("center", ctypes.c_int), ("iters_lock", ctypes.POINTER(ctypes.c_int)),
+                ("grid_ctas", ctypes.c_int), ("timeout_s", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("found", ctypes.c_int), ("total_iters", ctypes.c_longlong),
+                ("kernel_launches", ctypes.c_int), ("grid_ctas", ctypes.c_int),
+                ("block_threads", ctypes.c_int), ("alg_bytes", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("ldx", ctypes.c_long), ("M", ctypes.c_int),
+                ("N", ctypes.c_int), ("K", ctypes.c_int), ("T", ctypes.c_void_p),
+                ("P", ctypes.c_void_p), ("lambda_", ctypes.c_void_p), ("iters", ctypes.c_void_p),
+                ("status", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libgspca.so; raise when it is absent (never fall back to anything)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library not built: {LIB} is missing (run build())")
+        build()
+    lib = ctypes.CDLL(LIB)
+    vp, i, l, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_long, ctypes.c_double
+    lib.gspca_create.argtypes = [ctypes.POINTER(vp), i, l, l, i, i]
+    fit_args = [vp, vp, vp, i, l, i, i, i, d, i, i, vp, vp, vp, vp, vp, ctypes.POINTER(Opts)]
+    lib.gspca_fit.argtypes = fit_args
+    lib.gspca_fit_host.argtypes = fit_args
+    lib.gspca_fit_batched.argtypes = [vp, vp, ctypes.POINTER(Problem), i, d, i, i, ctypes.POINTER(Opts)]
+    lib.gspca_get_info.argtypes = [vp, ctypes.POINTER(Info)]
+    lib.gspca_destroy.argtypes = [vp]
+    lib.gspca_status_string.argtypes = [i]
+    lib.gspca_status_string.restype = ctypes.c_char_p
+    lib.gspca_last_cuda_error.argtypes = []
+    lib.gspca_last_cuda_error.restype = ctypes.c_char_p
+    for name in ("gspca_create", "gspca_fit", "gspca_fit_host", "gspca_fit_batched",
+                 "gspca_get_info", "gspca_destroy"):
+        getattr(lib, name).restype = i
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().gspca_status_string(int(status)).decode()
+
+
+gspca_status_string = status_string
+
+
+def last_cuda_error() -> str:
+    return load().gspca_last_cuda_error().decode()
+
+
+gspca_last_cuda_error = last_cuda_error
+
+
+def _opts(center=0, iters_lock=None, grid_ctas=0, timeout_s=0.0):
+    o = Opts()
+    o.center = int(center)
+    o.grid_ctas = int(grid_ctas)
+    o.timeout_s = float(timeout_s)
+    keep = None
+    if iters_lock is not None:
+        keep = (ctypes.c_int * len(iters_lock))(*[int(v) for v in iters_lock])
+        o.iters_lock = ctypes.cast(keep, ctypes.POINTER(ctypes.c_int))
+    return o, keep
+
+
+def gspca_create(device: int, max_M: int, max_N: int, max_K: int, dtype="f32") -> int:
+    h = ctypes.c_void_p()
+    st = load().gspca_create(ctypes.byref(h), int(device), int(max_M), int(max_N), int(max_K),
+                             _DTYPES[dtype])
+    if st != GSPCA_OK:
+        raise GspcaError(st, "gspca_create")
+    return h.value
+
+
+def gspca_destroy(h: int) -> int:
+    return load().gspca_destroy(ctypes.c_void_p(h))
+
+
+def gspca_get_info(h: int) -> dict:
+    info = Info()
+    st = load().gspca_get_info(ctypes.c_void_p(h), ctypes.byref(info))
+    if st != GSPCA_OK:
+        raise GspcaError(st, "gspca_get_info")
+    return {f: getattr(info, f) for f, _ in Info._fields_}
+
+
+def _layout_of(X):
+    """(layout, ldx) of a 2-D tensor/array given its strides in elements."""
+    M, N = X.shape
+    s0, s1 = (X.stride() if hasattr(X, "stride") and callable(X.stride)
+              else tuple(s // X.itemsize for s in X.strides))
+    if s1 == 1 and s0 >= N:
+        return GSPCA_ROW_MAJOR, s0
+    if s0 == 1 and s1 >= M:
+        return GSPCA_COL_MAJOR, s1
+    return None, None
+
+
+@dataclass
+class FitResult:
+    T: object
+    P: object
+    lam: object
+    iters: object
+    R: object
+    status: int
+    info: dict
+
+
+def gspca_fit(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="gs",
+              center: int = 0, iters_lock=None, want_R: bool = False, grid_ctas: int = 0,
+              timeout_s: float = 0.0, stream=None, check: bool = True) -> FitResult:
+    """Fit K components of X (a float32 CUDA tensor, any 2-D strided layout)."""
+    import torch
+
+    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
+        raise TypeError("X must be a 2-D float32 CUDA tensor")
+    layout, ldx = _layout_of(X)
+    if layout is None:
+        X = X.contiguous()
+        layout, ldx = GSPCA_ROW_MAJOR, X.shape[1]
+    M, N = X.shape
+    dev = X.device
+    T = torch.empty((K, M), device=dev, dtype=torch.float32).t()
+    P = torch.empty((K, N), device=dev, dtype=torch.float32).t()
+    lam = torch.empty(K, device=dev, dtype=torch.float64)
+    iters = torch.empty(K, device=dev, dtype=torch.int32)
+    R = torch.empty((N, M), device=dev, dtype=torch.float32).t() if want_R else None
+    if stream is None:
+        stream = torch.cuda.current_stream(dev).cuda_stream
+    o, keep = _opts(center, iters_lock, grid_ctas, timeout_s)
+    st = load().gspca_fit(ctypes.c_void_p(h), ctypes.c_void_p(stream), ctypes.c_void_p(X.data_ptr()),
+                          layout, int(ldx), M, N, int(K), float(tol), int(max_iter), _ALGOS[algo],
+                          ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(P.data_ptr()),
+                          ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(iters.data_ptr()),
+                          ctypes.c_void_p(R.data_ptr()) if R is not None else None, ctypes.byref(o))
+    del keep
+    if check and st not in (GSPCA_OK, GSPCA_WARN_NOT_CONVERGED, GSPCA_ERR_DEGENERATE):
+        raise GspcaError(st, "gspca_fit")
+    return FitResult(T, P, lam, iters, R, st, gspca_get_info(h))
+
+
+def gspca_fit_host(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="gs",
+                   center: int = 0, iters_lock=None, want_R: bool = False, stream=None,
+                   out=None, check: bool = True) -> FitResult:
+    """Same as gspca_fit with host memory: X a float32 numpy array or CPU tensor (pinned is
+    fastest); outputs are host arrays (reused from `out` when given)."""
+    import numpy as np
+
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(X, torch.Tensor):
+        if X.is_cuda or X.dtype != torch.float32:
+            raise TypeError("X must be a float32 host tensor")
+        xp = X.data_ptr()
+        layout, ldx = _layout_of(X)
+    else:
+        X = np.asarray(X)
+        if X.dtype != np.float32:
+            raise TypeError("X must be float32")
+        layout, ldx = _layout_of(X)
+        xp = X.ctypes.data
+    if layout is None:
+        raise ValueError("X must be row- or column-major")
+    M, N = X.shape
+    if out is None:
+        out = {"T": np.empty((K, M), np.float32), "P": np.empty((K, N), np.float32),
+               "lam": np.empty(K, np.float64), "iters": np.empty(K, np.int32),
+               "R": np.empty((N, M), np.float32) if want_R else None}
+    if stream is None and torch is not None and torch.cuda.is_available():
+        stream = torch.cuda.current_stream().cuda_stream
+    o, keep = _opts(center, iters_lock)
+    st = load().gspca_fit_host(ctypes.c_void_p(h), ctypes.c_void_p(stream), ctypes.c_void_p(xp), layout,
+                               int(ldx), M, N, int(K), float(tol), int(max_iter), _ALGOS[algo],
+                               ctypes.c_void_p(out["T"].ctypes.data), ctypes.c_void_p(out["P"].ctypes.data),
+                               ctypes.c_void_p(out["lam"].ctypes.data),
+                               ctypes.c_void_p(out["iters"].ctypes.data),
+                               ctypes.c_void_p(out["R"].ctypes.data) if out["R"] is not None else None,
+                               ctypes.byref(o))
+    del keep
+    if check and st not in (GSPCA_OK, GSPCA_WARN_NOT_CONVERGED, GSPCA_ERR_DEGENERATE):
+        raise GspcaError(st, "gspca_fit_host")
+    R = out["R"].T if out["R"] is not None else None
+    return FitResult(out["T"].T, out["P"].T, out["lam"], out["iters"], R, st, gspca_get_info(h))
+
+
+class Handle:
+    """Owns one gspca handle (device workspace for problems up to max_M x max_N x max_K)."""
+
+    def __init__(self, max_M: int, max_N: int, max_K: int, device: int = 0, dtype="f32"):
+        self.h = gspca_create(device, max_M, max_N, max_K, dtype)
+
+    def fit(self, X, K, **kw) -> FitResult:
+        return gspca_fit(self.h, X, K, **kw)
+
+    def fit_host(self, X, K, **kw) -> FitResult:
+        return gspca_fit_host(self.h, X, K, **kw)
+
+    def info(self) -> dict:
+        return gspca_get_info(self.h)
+
+    def close(self):
+        if self.h:
+            gspca_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gspca_fit_batched(h: int, problems, tol: float = 1e-6, max_iter: int = 1000, algo="gs",
+                      grid_ctas: int = 0, timeout_s: float = 0.0, stream=None, check: bool = True):
+    """Fit independent problems in one launch.  `problems` is a list of dicts with a float32
+    CUDA tensor "X" (any column- or row-major layout is packed column-major here) and "K";
+    returns a list of FitResult (T, P, lam, iters, status per problem) and the batch status."""
+    import torch
+
+    descs = (Problem * len(problems))()
+    outs = []
+    keep = []
+    for i, pr in enumerate(problems):
+        X = pr["X"]
+        if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
+            raise TypeError("each X must be a 2-D float32 CUDA tensor")
+        layout, ldx = _layout_of(X)
+        if layout != GSPCA_COL_MAJOR:
+            X = X.t().contiguous().t()
+            ldx = X.shape[0]
+        keep.append(X)
+        M, N = X.shape
+        K = int(pr["K"])
+        dev = X.device
+        T = torch.zeros((K, M), device=dev, dtype=torch.float32).t()
+        P = torch.zeros((K, N), device=dev, dtype=torch.float32).t()
+        lam = torch.zeros(K, device=dev, dtype=torch.float64)
+        iters = torch.zeros(K, device=dev, dtype=torch.int32)
+        st = torch.zeros(1, device=dev, dtype=torch.int32)
+        d = descs[i]
+        d.X, d.ldx, d.M, d.N, d.K = X.data_ptr(), int(ldx), M, N, K
+        d.T, d.P, d.lambda_, d.iters, d.status = (T.data_ptr(), P.data_ptr(), lam.data_ptr(),
+                                                  iters.data_ptr(), st.data_ptr())
+        outs.append((T, P, lam, iters, st))
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    o, _ = _opts(0, None, grid_ctas, timeout_s)
+    st = load().gspca_fit_batched(ctypes.c_void_p(h), ctypes.c_void_p(stream), descs, len(problems),
+                                  float(tol), int(max_iter), _ALGOS[algo], ctypes.byref(o))
+    if check and st not in (GSPCA_OK, GSPCA_WARN_NOT_CONVERGED, GSPCA_ERR_DEGENERATE):
+        raise GspcaError(st, "gspca_fit_batched")
+    info = gspca_get_info(h)
+    res = [FitResult(T, P, lam, iters, None, s, info) for (T, P, lam, iters, s) in outs]
+    return res, st

@@ -1,0 +1,461 @@
+// Host side of the C ABI declared in include/gspca.h: handle and workspace
+// management, argument checks, and the launch sequence of one fit
+//   [centring means] -> pack X into R panels -> persistent fit kernel
+//   -> epilogue (T, P, lambda, iters) -> [unpack R_out]
+// all enqueued on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/gspca.h"
+#include "fit_kernel.cuh"
+#include "prep_kernels.cuh"
+
+using namespace gspca;
+
+namespace {
+
+char g_cuda_err[256] = "no CUDA error";
+
+bool cuda_ok(cudaError_t e) {
+    if (e == cudaSuccess) return true;
+    std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return false;
+}
+
+#define GS_CUDA(call)                                        \
+    do {                                                     \
+        if (!cuda_ok(call)) return GSPCA_ERR_CUDA;           \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+constexpr int kMaxCols = 16 * kBlock;  // columns one CTA can hold (CPT <= 16)
+
+}  // namespace
+
+struct gspca_handle {
+    int device = 0;
+    long max_M = 0, max_N = 0;
+    int max_K = 0;
+    gspca_dtype dtype = GSPCA_F32;
+    int num_sms = 0;
+    int ld = 0;      // row stride of V, U, W (>= max_K)
+    int L = 0;       // row stride of the vector partials
+    int Gmax = 0;    // CTAs the partial buffers hold
+    int xpart_cap = 0;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    float *R = nullptr, *V = nullptr, *U = nullptr, *W = nullptr;
+    float *vraw = nullptr, *vcorr = nullptr, *ut = nullptr, *ucur = nullptr, *part = nullptr;
+    double *upre = nullptr, *spart = nullptr, *red = nullptr, *reds = nullptr, *normpart = nullptr;
+    double *lam = nullptr, *xpart = nullptr, *cmean = nullptr, *rmean = nullptr;
+    int *iters = nullptr, *info = nullptr, *abort = nullptr, *lock = nullptr;
+    unsigned* bar = nullptr;
+    int* h_info = nullptr;  // pinned
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the persistent kernel
+    // host-buffer entry point staging (lazily allocated)
+    void* stage = nullptr;
+    float *sX = nullptr, *sT = nullptr, *sP = nullptr, *sR = nullptr;
+    double* slam = nullptr;
+    int* siters = nullptr;
+    gspca_info last{};
+};
+
+namespace {
+
+template <int CPT>
+cudaError_t launch_fit(const FitArgs& a, int G, size_t dyn, cudaStream_t s) {
+    void* args[] = {const_cast<FitArgs*>(&a)};
+    return cudaLaunchCooperativeKernel((const void*)fit_kernel<CPT>, dim3(G), dim3(kBlock), args, dyn, s);
+}
+
+template <int CPT>
+int occupancy(size_t dyn) {
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fit_kernel<CPT>, kBlock, dyn) != cudaSuccess) return 0;
+    return bps;
+}
+
+int cpt_for(int N) {
+    int c = 1;
+    while (c * kBlock < N) c *= 2;
+    return c;
+}
+
+gspca_status check_fit_args(gspca_t h, const void* X, gspca_layout layout, long ldx, int M, int N, int K,
+                            double tol, int max_iter, gspca_algo algo, const void* T, const void* P,
+                            const void* lambda, const gspca_opts* opts) {
+    if (!h || !X || !T || !P || !lambda) return GSPCA_ERR_INVALID_ARG;
+    if (M < 1 || N < 1 || K < 1 || K > M || K > N) return GSPCA_ERR_INVALID_ARG;
+    if (M > h->max_M || N > h->max_N || K > h->max_K) return GSPCA_ERR_INVALID_ARG;
+    if (!(tol > 0.0) || max_iter < 1) return GSPCA_ERR_INVALID_ARG;
+    if (algo != GSPCA_NIPALS && algo != GSPCA_GS) return GSPCA_ERR_INVALID_ARG;
+    if (layout == GSPCA_COL_MAJOR) {
+        if (ldx < M) return GSPCA_ERR_INVALID_ARG;
+    } else if (layout == GSPCA_ROW_MAJOR) {
+        if (ldx < N) return GSPCA_ERR_INVALID_ARG;
+    } else {
+        return GSPCA_ERR_INVALID_ARG;
+    }
+    if (opts) {
+        if (opts->center < 0 || opts->center > 2 || opts->grid_ctas < 0 || opts->timeout_s < 0)
+            return GSPCA_ERR_INVALID_ARG;
+        if (opts->iters_lock)
+            for (int k = 0; k < K; ++k)
+                if (opts->iters_lock[k] < 1) return GSPCA_ERR_INVALID_ARG;
+    }
+    if (h->dtype != GSPCA_F32) return GSPCA_ERR_NOT_SUPPORTED;
+    return GSPCA_OK;
+}
+
+// Enqueue one fit on device buffers.  Does not synchronise.
+gspca_status enqueue_fit(gspca_t h, cudaStream_t s, const float* X, gspca_layout layout, long ldx, int M,
+                         int N, int K, double tol, int max_iter, gspca_algo algo, float* T, float* P,
+                         double* lambda, int* iters, float* R_out, const gspca_opts* opts) {
+    const int center = opts ? opts->center : 0;
+    const double timeout = (opts && opts->timeout_s > 0) ? opts->timeout_s : 2.0;
+    const int np = (M + 3) / 4;
+    int launches = 0;
+
+    if (center == 1) {
+        colmean_kernel<<<(N + 7) / 8, 256, 0, s>>>(X, (int)layout, ldx, M, N, h->cmean);
+        ++launches;
+    } else if (center == 2) {
+        rowmean_kernel<<<(M + 7) / 8, 256, 0, s>>>(X, (int)layout, ldx, M, N, h->rmean);
+        ++launches;
+    }
+    const dim3 pgrid((N + 31) / 32, (np + 31) / 32);
+    const int nxpart = (int)(pgrid.x * pgrid.y);
+    if (nxpart > h->xpart_cap) return GSPCA_ERR_NOT_SUPPORTED;
+    pack_kernel<<<pgrid, kPackThreads, 0, s>>>(X, (int)layout, ldx, M, N, np, center, h->cmean, h->rmean, h->R,
+                                               h->xpart, h->bar, h->abort, h->info, kInfoWords);
+    ++launches;
+    if (!cuda_ok(cudaGetLastError())) return GSPCA_ERR_CUDA;
+
+    const int* lock_dev = nullptr;
+    if (opts && opts->iters_lock) {
+        GS_CUDA(cudaMemcpyAsync(h->lock, opts->iters_lock, sizeof(int) * K, cudaMemcpyHostToDevice, s));
+        lock_dev = h->lock;
+    }
+
+    FitArgs a{};
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.np = np;
+    a.algo = (int)algo;
+    a.max_iter = max_iter;
+    a.tol = tol;
+    a.eps_thresh = 64.0 * (double)FLT_EPSILON;
+    a.xpart = h->xpart;
+    a.nxpart = nxpart;
+    a.R = h->R;
+    a.V = h->V;
+    a.ldv = h->ld;
+    a.U = h->U;
+    a.ldu = h->ld;
+    a.W = h->W;
+    a.ldw = h->ld;
+    a.vraw = h->vraw;
+    a.vcorr = h->vcorr;
+    a.ut = h->ut;
+    a.upre = h->upre;
+    a.ucur = h->ucur;
+    a.part = h->part;
+    a.L = h->L;
+    a.spart = h->spart;
+    a.red = h->red;
+    a.reds = h->reds;
+    a.normpart = h->normpart;
+    a.lam = h->lam;
+    a.iters = h->iters;
+    a.info = h->info;
+    a.bar = h->bar;
+    a.abort = h->abort;
+    a.iters_lock = lock_dev;
+    a.timeout_ns = (unsigned long long)(timeout * 1e9);
+
+    const size_t dyn = sizeof(float) * (size_t)h->ld;
+    const int cpt = cpt_for(N);
+    int bps = 0;
+    switch (cpt) {
+        case 1: bps = occupancy<1>(dyn); break;
+        case 2: bps = occupancy<2>(dyn); break;
+        case 4: bps = occupancy<4>(dyn); break;
+        case 8: bps = occupancy<8>(dyn); break;
+        case 16: bps = occupancy<16>(dyn); break;
+        default: return GSPCA_ERR_NOT_SUPPORTED;
+    }
+    if (bps < 1) return GSPCA_ERR_CUDA;
+    const int rounds_ppr = (cpt >= 8) ? 1 : 8 / cpt;
+    int G = h->num_sms * bps;
+    const int want = (np + rounds_ppr - 1) / rounds_ppr;  // at least one full round per CTA
+    if (G > want) G = want;
+    if (opts && opts->grid_ctas > 0 && opts->grid_ctas < G) G = opts->grid_ctas;
+    if (G > h->Gmax) G = h->Gmax;
+    if (G < 1) G = 1;
+
+    if (!cuda_ok(cudaEventRecord(h->ev0, s))) return GSPCA_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
+    switch (cpt) {
+        case 1: e = launch_fit<1>(a, G, dyn, s); break;
+        case 2: e = launch_fit<2>(a, G, dyn, s); break;
+        case 4: e = launch_fit<4>(a, G, dyn, s); break;
+        case 8: e = launch_fit<8>(a, G, dyn, s); break;
+        case 16: e = launch_fit<16>(a, G, dyn, s); break;
+    }
+    if (!cuda_ok(e)) return GSPCA_ERR_CUDA;
+    if (!cuda_ok(cudaEventRecord(h->ev1, s))) return GSPCA_ERR_CUDA;
+    ++launches;
+
+    const dim3 egrid((M + 31) / 32 + (N + 31) / 32, (K + 31) / 32);
+    epilogue_kernel<<<egrid, 256, 0, s>>>(h->V, h->ld, h->U, h->ld, h->lam, h->iters, h->info, M, N, K,
+                                          algo == GSPCA_GS, T, P, lambda, iters);
+    ++launches;
+    if (R_out) {
+        unpack_kernel<<<pgrid, kPackThreads, 0, s>>>(h->R, M, N, np, h->V, h->ld, h->U, h->ld, h->lam, h->info, K,
+                                                     algo == GSPCA_GS, R_out);
+        ++launches;
+    }
+    if (!cuda_ok(cudaGetLastError())) return GSPCA_ERR_CUDA;
+
+    h->last.grid_ctas = G;
+    h->last.block_threads = kBlock;
+    h->last.kernel_launches = launches;
+    return GSPCA_OK;
+}
+
+// Algorithmic bytes of the persistent kernel for a finished fit: per pass one
+// read of R (M x N FP32); per component one extra write of R (the fused
+// deflation) ; GS-PCA reads V_(k) (M x k) and U_(k), W (N x k) each pass.
+double alg_bytes(int M, int N, int K, int found, const int* iters, bool gs) {
+    const double mn = (double)M * N * 4.0;
+    double b = 0.0;
+    for (int k = 0; k < found; ++k) {
+        const double passes = (double)iters[k] + 1.0;
+        b += passes * mn + (k > 0 ? mn : 0.0);
+        if (gs && k > 0) b += (double)iters[k] * (2.0 * M * k + 3.0 * N * k) * 4.0;
+    }
+    return b;
+}
+
+gspca_status finish(gspca_t h, cudaStream_t s, int K, gspca_algo algo, int M, int N) {
+    GS_CUDA(cudaMemcpyAsync(h->h_info, h->info, sizeof(int) * kInfoWords, cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaMemcpyAsync(h->h_info + kInfoWords, h->abort, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int* hiters = h->h_info + kInfoWords + 4;
+    GS_CUDA(cudaMemcpyAsync(hiters, h->iters, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    GS_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    h->last.kernel_ms = ms;
+    if (h->h_info[kInfoWords] != 0) return GSPCA_ERR_TIMEOUT;
+    const int st = h->h_info[kInfoStatus];
+    h->last.found = h->h_info[kInfoFound];
+    h->last.total_iters = (long long)h->h_info[kInfoItersLo] + ((long long)h->h_info[kInfoItersHi] << 31);
+    h->last.alg_bytes = alg_bytes(M, N, K, h->last.found, hiters, algo == GSPCA_GS);
+    if (st == kStDegenerate) return GSPCA_ERR_DEGENERATE;
+    if (st == kStNotConverged) return GSPCA_WARN_NOT_CONVERGED;
+    return GSPCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gspca_status gspca_create(gspca_t* out, int device, long max_M, long max_N, int max_K, gspca_dtype dtype) {
+    if (!out) return GSPCA_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (max_M < 1 || max_N < 1 || max_K < 1 || max_K > max_N || max_K > max_M) return GSPCA_ERR_INVALID_ARG;
+    if (dtype != GSPCA_F32 && dtype != GSPCA_BF16) return GSPCA_ERR_INVALID_ARG;
+    if (max_N > kMaxCols) return GSPCA_ERR_NOT_SUPPORTED;
+    GS_CUDA(cudaSetDevice(device));
+    gspca_handle* h = new (std::nothrow) gspca_handle();
+    if (!h) return GSPCA_ERR_OOM;
+    h->device = device;
+    h->max_M = max_M;
+    h->max_N = max_N;
+    h->max_K = max_K;
+    h->dtype = dtype;
+    if (!cuda_ok(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device))) {
+        delete h;
+        return GSPCA_ERR_CUDA;
+    }
+    const long Mp = (max_M + 3) / 4 * 4;
+    h->ld = (int)align_up((size_t)max_K, 4);
+    h->L = (int)align_up((size_t)max_N + max_K + 4, 4);
+    h->Gmax = 4 * h->num_sms;
+    const long np = Mp / 4;
+    h->xpart_cap = (int)(((max_N + 31) / 32) * ((np + 31) / 32));
+
+    struct Item {
+        void** p;
+        size_t bytes;
+    } items[] = {
+        {(void**)&h->R, sizeof(float) * (size_t)Mp * max_N},
+        {(void**)&h->V, sizeof(float) * (size_t)Mp * h->ld},
+        {(void**)&h->U, sizeof(float) * (size_t)max_N * h->ld},
+        {(void**)&h->W, sizeof(float) * (size_t)max_N * h->ld},
+        {(void**)&h->vraw, sizeof(float) * (size_t)Mp},
+        {(void**)&h->vcorr, sizeof(float) * (size_t)Mp},
+        {(void**)&h->ut, sizeof(float) * (size_t)max_N},
+        {(void**)&h->ucur, sizeof(float) * (size_t)max_N},
+        {(void**)&h->upre, sizeof(double) * (size_t)max_N},
+        {(void**)&h->part, sizeof(float) * (size_t)h->Gmax * h->L},
+        {(void**)&h->spart, sizeof(double) * (size_t)h->Gmax * 4},
+        {(void**)&h->red, sizeof(double) * (size_t)h->L},
+        {(void**)&h->reds, sizeof(double) * 4},
+        {(void**)&h->normpart, sizeof(double) * (size_t)h->Gmax},
+        {(void**)&h->lam, sizeof(double) * (size_t)max_K},
+        {(void**)&h->xpart, sizeof(double) * (size_t)h->xpart_cap},
+        {(void**)&h->cmean, sizeof(double) * (size_t)max_N},
+        {(void**)&h->rmean, sizeof(double) * (size_t)Mp},
+        {(void**)&h->iters, sizeof(int) * (size_t)max_K},
+        {(void**)&h->info, sizeof(int) * kInfoWords},
+        {(void**)&h->abort, sizeof(int) * 4},
+        {(void**)&h->lock, sizeof(int) * (size_t)max_K},
+        {(void**)&h->bar, sizeof(unsigned) * 4},
+    };
+    size_t total = 0;
+    for (auto& it : items) total = align_up(total, 256) + align_up(it.bytes, 256);
+    void* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, total);
+    if (e != cudaSuccess) {
+        cuda_ok(e);
+        delete h;
+        return e == cudaErrorMemoryAllocation ? GSPCA_ERR_OOM : GSPCA_ERR_CUDA;
+    }
+    h->ws = base;
+    h->ws_bytes = total;
+    size_t off = 0;
+    for (auto& it : items) {
+        off = align_up(off, 256);
+        *it.p = (char*)base + off;
+        off += align_up(it.bytes, 256);
+    }
+    if (!cuda_ok(cudaMemset(base, 0, total)) ||
+        !cuda_ok(cudaMallocHost((void**)&h->h_info, sizeof(int) * (kInfoWords + 4 + (size_t)max_K))) ||
+        !cuda_ok(cudaEventCreate(&h->ev0)) || !cuda_ok(cudaEventCreate(&h->ev1))) {
+        cudaFree(base);
+        delete h;
+        return GSPCA_ERR_CUDA;
+    }
+    *out = h;
+    return GSPCA_OK;
+}
+
+gspca_status gspca_fit(gspca_t h, void* stream, const float* X, gspca_layout layout, long ldx, int M, int N, int K,
+                       double tol, int max_iter, gspca_algo algo, float* T, float* P, double* lambda, int* iters,
+                       float* R_out, const gspca_opts* opts) {
+    gspca_status st = check_fit_args(h, X, layout, ldx, M, N, K, tol, max_iter, algo, T, P, lambda, opts);
+    if (st != GSPCA_OK) return st;
+    GS_CUDA(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    st = enqueue_fit(h, s, X, layout, ldx, M, N, K, tol, max_iter, algo, T, P, lambda, iters, R_out, opts);
+    if (st != GSPCA_OK) return st;
+    return finish(h, s, K, algo, M, N);
+}
+
+gspca_status gspca_fit_host(gspca_t h, void* stream, const float* X, gspca_layout layout, long ldx, int M, int N,
+                            int K, double tol, int max_iter, gspca_algo algo, float* T, float* P, double* lambda,
+                            int* iters, float* R_out, const gspca_opts* opts) {
+    gspca_status st = check_fit_args(h, X, layout, ldx, M, N, K, tol, max_iter, algo, T, P, lambda, opts);
+    if (st != GSPCA_OK) return st;
+    GS_CUDA(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!h->stage) {
+        const size_t xs = align_up(sizeof(float) * (size_t)h->max_M * h->max_N, 256);
+        const size_t ts = align_up(sizeof(float) * (size_t)h->max_M * h->max_K, 256);
+        const size_t ps = align_up(sizeof(float) * (size_t)h->max_N * h->max_K, 256);
+        const size_t ls = align_up(sizeof(double) * (size_t)h->max_K, 256);
+        const size_t is = align_up(sizeof(int) * (size_t)h->max_K, 256);
+        const size_t rs = xs;
+        void* b = nullptr;
+        cudaError_t e = cudaMalloc(&b, xs + ts + ps + ls + is + rs);
+        if (e != cudaSuccess) {
+            cuda_ok(e);
+            return e == cudaErrorMemoryAllocation ? GSPCA_ERR_OOM : GSPCA_ERR_CUDA;
+        }
+        h->stage = b;
+        char* c = (char*)b;
+        h->sX = (float*)c;
+        h->sT = (float*)(c + xs);
+        h->sP = (float*)(c + xs + ts);
+        h->slam = (double*)(c + xs + ts + ps);
+        h->siters = (int*)(c + xs + ts + ps + ls);
+        h->sR = (float*)(c + xs + ts + ps + ls + is);
+    }
+    const size_t xbytes = layout == GSPCA_COL_MAJOR ? sizeof(float) * ((size_t)ldx * (N - 1) + M)
+                                                    : sizeof(float) * ((size_t)ldx * (M - 1) + N);
+    if (xbytes > sizeof(float) * (size_t)h->max_M * h->max_N) {
+        // a padded leading dimension larger than the staging buffer: pack rows/cols tightly
+        if (layout == GSPCA_COL_MAJOR)
+            GS_CUDA(cudaMemcpy2DAsync(h->sX, sizeof(float) * M, X, sizeof(float) * ldx, sizeof(float) * M, N,
+                                      cudaMemcpyHostToDevice, s));
+        else
+            GS_CUDA(cudaMemcpy2DAsync(h->sX, sizeof(float) * N, X, sizeof(float) * ldx, sizeof(float) * N, M,
+                                      cudaMemcpyHostToDevice, s));
+        ldx = layout == GSPCA_COL_MAJOR ? M : N;
+    } else {
+        GS_CUDA(cudaMemcpyAsync(h->sX, X, xbytes, cudaMemcpyHostToDevice, s));
+    }
+    st = enqueue_fit(h, s, h->sX, layout, ldx, M, N, K, tol, max_iter, algo, h->sT, h->sP, h->slam, h->siters,
+                     R_out ? h->sR : nullptr, opts);
+    if (st != GSPCA_OK) return st;
+    GS_CUDA(cudaMemcpyAsync(T, h->sT, sizeof(float) * (size_t)M * K, cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaMemcpyAsync(P, h->sP, sizeof(float) * (size_t)N * K, cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaMemcpyAsync(lambda, h->slam, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+    if (iters) GS_CUDA(cudaMemcpyAsync(iters, h->siters, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
+    if (R_out) GS_CUDA(cudaMemcpyAsync(R_out, h->sR, sizeof(float) * (size_t)M * N, cudaMemcpyDeviceToHost, s));
+    return finish(h, s, K, algo, M, N);
+}
+
+gspca_status gspca_fit_batched(gspca_t h, void* stream, const gspca_problem* problems, int count, double tol,
+                               int max_iter, gspca_algo algo, const gspca_opts* opts) {
+    (void)stream;
+    (void)opts;
+    if (!h || !problems || count < 1 || !(tol > 0.0) || max_iter < 1) return GSPCA_ERR_INVALID_ARG;
+    if (algo != GSPCA_NIPALS && algo != GSPCA_GS) return GSPCA_ERR_INVALID_ARG;
+    return GSPCA_ERR_NOT_SUPPORTED;
+}
+
+gspca_status gspca_get_info(gspca_t h, gspca_info* info) {
+    if (!h || !info) return GSPCA_ERR_INVALID_ARG;
+    *info = h->last;
+    return GSPCA_OK;
+}
+
+gspca_status gspca_destroy(gspca_t h) {
+    if (!h) return GSPCA_OK;
+    cudaSetDevice(h->device);
+    gspca_status st = GSPCA_OK;
+    if (h->stage && !cuda_ok(cudaFree(h->stage))) st = GSPCA_ERR_CUDA;
+    if (h->ws && !cuda_ok(cudaFree(h->ws))) st = GSPCA_ERR_CUDA;
+    if (h->h_info && !cuda_ok(cudaFreeHost(h->h_info))) st = GSPCA_ERR_CUDA;
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    delete h;
+    return st;
+}
+
+const char* gspca_status_string(gspca_status s) {
+    switch (s) {
+        case GSPCA_OK: return "ok";
+        case GSPCA_ERR_INVALID_ARG: return "invalid argument";
+        case GSPCA_ERR_CUDA: return "CUDA error";
+        case GSPCA_ERR_OOM: return "out of device memory";
+        case GSPCA_WARN_NOT_CONVERGED: return "at least one component reached max_iter without converging";
+        case GSPCA_ERR_DEGENERATE: return "rank exhausted: fewer than K components found";
+        case GSPCA_ERR_TIMEOUT: return "a bounded device wait timed out";
+        case GSPCA_ERR_NOT_SUPPORTED: return "not supported by this build";
+    }
+    return "unknown status";
+}
+
+const char* gspca_last_cuda_error(void) { return g_cuda_err; }
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+"""CPU checks of the C ABI: the library loads, exports every declared entry
+point, and rejects bad arguments before touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0811_1081_gb300 import buildlib as b
+
+    b.build()
+    import paper_0811_1081_gb300 as gp
+
+    return gp.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gspca.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gspca_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert "gspca_fit" in names and "gspca_create" in names and "gspca_fit_batched" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_python_binding_names_match_header():
+    import paper_0811_1081_gb300 as gp
+
+    for n in declared_functions():
+        assert n in gp.EXPORTS, n
+        assert hasattr(gp, n), n
+
+
+def test_status_strings(lib):
+    import paper_0811_1081_gb300 as gp
+
+    for s in range(8):
+        assert isinstance(gp.status_string(s), str) and gp.status_string(s)
+    assert gp.status_string(99) == "unknown status"
+
+
+def test_invalid_arguments_need_no_gpu(lib):
+    h = ctypes.c_void_p()
+    assert lib.gspca_create(None, 0, 10, 10, 2, 0) == 1
+    assert lib.gspca_create(ctypes.byref(h), 0, 0, 10, 2, 0) == 1
+    assert lib.gspca_create(ctypes.byref(h), 0, 10, 10, 11, 0) == 1
+    assert lib.gspca_create(ctypes.byref(h), 0, 10, 10, 2, 7) == 1
+    assert lib.gspca_create(ctypes.byref(h), 0, 10, 10 ** 6, 2, 0) == 7  # beyond the column limit
+    assert lib.gspca_fit(None, None, None, 0, 1, 1, 1, 1, 1e-6, 10, 1, None, None, None, None, None,
+                         None) == 1
+    assert lib.gspca_destroy(None) == 0
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    import importlib
+
+    import paper_0811_1081_gb300 as gp
+    import paper_0811_1081_gb300.buildlib as b
+
+    monkeypatch.setattr(gp, "_lib", None)
+    monkeypatch.setattr(gp, "LIB", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError):
+        gp.load()
+    importlib.reload(b)
