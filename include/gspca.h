@@ -145,6 +145,38 @@ typedef struct {
 gspca_status gspca_fit_batched(gspca_t h, void *stream, const gspca_problem *problems, int count,
                                double tol, int max_iter, gspca_algo algo, const gspca_opts *opts);
 
+/* Fit without allocating.  The paper has no counterpart to this entry point;
+ * it exists for callers that must not allocate device memory themselves or
+ * through the library: for example a plug-in running inside an application
+ * whose own allocator owns the device memory (an outside cudaMalloc can fail
+ * or break that allocator's budget), or a latency-critical loop that cannot
+ * afford a cudaMalloc/cudaFree pair (cudaFree can synchronise the device).
+ *
+ * Same computation and conventions as gspca_fit (device pointers for X, T,
+ * P, lambda, iters, R_out), but no handle: the scratch workspace is a
+ * file-scope device array of GSPCA_NOALLOC_SCRATCH_BYTES bytes inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  The call runs on the current device and never calls cudaMalloc,
+ * cudaFree or any allocating routine.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array and leaves its contents behind; the
+ *     words that must start at zero (grid barrier, abort flag, status) are
+ *     cleared by the call's own first kernel.  Calls whose work overlaps on
+ *     the GPU (other streams, other host threads) race on the array: order
+ *     them on one stream or synchronise between them.
+ *   - Limit: the scratch this problem needs (about 4*(M+3)*(N+K) +
+ *     8*(M+N)*(K+2) bytes plus per-CTA partial sums) must fit in
+ *     GSPCA_NOALLOC_SCRATCH_BYTES; otherwise the call returns
+ *     GSPCA_ERR_NOT_SUPPORTED and launches nothing.  Other errors as for
+ *     gspca_fit.  The call synchronises `stream` before returning. */
+#define GSPCA_NOALLOC_SCRATCH_BYTES (64u << 20)
+gspca_status gspca_fit_noalloc(void *stream, const float *X, gspca_layout layout, long ldx, int M,
+                               int N, int K, double tol, int max_iter, gspca_algo algo, float *T,
+                               float *P, double *lambda, int *iters, float *R_out,
+                               const gspca_opts *opts);
+
 /* Record of the last call on h. */
 gspca_status gspca_get_info(gspca_t h, gspca_info *info);
 

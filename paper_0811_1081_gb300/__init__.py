@@ -31,7 +31,7 @@ GSPCA_ERR_TIMEOUT = 6
 GSPCA_ERR_NOT_SUPPORTED = 7
 
 EXPORTS = ["gspca_create", "gspca_fit", "gspca_fit_host", "gspca_fit_batched", "gspca_get_info",
-           "gspca_destroy", "gspca_status_string", "gspca_last_cuda_error"]
+           "gspca_destroy", "gspca_status_string", "gspca_last_cuda_error", "gspca_fit_noalloc"]
 
 _ALGOS = {"nipals": GSPCA_NIPALS, "gs": GSPCA_GS, GSPCA_NIPALS: GSPCA_NIPALS, GSPCA_GS: GSPCA_GS}
 _DTYPES = {"f32": GSPCA_F32, "bf16": GSPCA_BF16, GSPCA_F32: GSPCA_F32, GSPCA_BF16: GSPCA_BF16}
@@ -84,6 +84,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.gspca_fit.argtypes = fit_args
     lib.gspca_fit_host.argtypes = fit_args
     lib.gspca_fit_batched.argtypes = [vp, vp, ctypes.POINTER(Problem), i, d, i, i, ctypes.POINTER(Opts)]
+    lib.gspca_fit_noalloc.argtypes = fit_args[1:]
+    lib.gspca_fit_noalloc.restype = i
     lib.gspca_get_info.argtypes = [vp, ctypes.POINTER(Info)]
     lib.gspca_destroy.argtypes = [vp]
     lib.gspca_status_string.argtypes = [i]
@@ -321,3 +323,43 @@ def gspca_fit_batched(h: int, problems, tol: float = 1e-6, max_iter: int = 1000,
     info = gspca_get_info(h)
     res = [FitResult(T, P, lam, iters, None, s, info) for (T, P, lam, iters, s) in outs]
     return res, st
+
+
+NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def gspca_fit_noalloc(X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="gs", center: int = 0,
+                      iters_lock=None, want_R: bool = False, stream=None, check: bool = True) -> FitResult:
+    """gspca_fit without a handle and without any device allocation inside the library: the
+    workspace is the library's fixed scratch array (NOALLOC_SCRATCH_BYTES per device).  For
+    callers that must not allocate device memory.  Output tensors are the caller's (allocated
+    here by PyTorch, outside the library)."""
+    import torch
+
+    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
+        raise TypeError("X must be a 2-D float32 CUDA tensor")
+    layout, ldx = _layout_of(X)
+    if layout is None:
+        X = X.contiguous()
+        layout, ldx = GSPCA_ROW_MAJOR, X.shape[1]
+    M, N = X.shape
+    dev = X.device
+    T = torch.empty((K, M), device=dev, dtype=torch.float32).t()
+    P = torch.empty((K, N), device=dev, dtype=torch.float32).t()
+    lam = torch.empty(K, device=dev, dtype=torch.float64)
+    iters = torch.empty(K, device=dev, dtype=torch.int32)
+    R = torch.empty((N, M), device=dev, dtype=torch.float32).t() if want_R else None
+    if stream is None:
+        stream = torch.cuda.current_stream(dev).cuda_stream
+    o, keep = _opts(center, iters_lock)
+    with torch.cuda.device(dev):
+        st = load().gspca_fit_noalloc(ctypes.c_void_p(stream), ctypes.c_void_p(X.data_ptr()), layout, int(ldx),
+                                      M, N, int(K), float(tol), int(max_iter), _ALGOS[algo],
+                                      ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(P.data_ptr()),
+                                      ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(iters.data_ptr()),
+                                      ctypes.c_void_p(R.data_ptr()) if R is not None else None,
+                                      ctypes.byref(o))
+    del keep
+    if check and st not in (GSPCA_OK, GSPCA_WARN_NOT_CONVERGED, GSPCA_ERR_DEGENERATE):
+        raise GspcaError(st, "gspca_fit_noalloc")
+    return FitResult(T, P, lam, iters, R, st, {})

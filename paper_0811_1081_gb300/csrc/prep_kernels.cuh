@@ -14,7 +14,7 @@ __device__ __forceinline__ float load_x(const float* X, int layout, long ldx, in
 }
 
 // mean over rows of every column (warp per column), FP64 sums.
-__global__ void colmean_kernel(const float* X, int layout, long ldx, int M, int N, double* mean) {
+static __global__ void colmean_kernel(const float* X, int layout, long ldx, int M, int N, double* mean) {
     const int lane = threadIdx.x & 31;
     const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (c >= N) return;
@@ -25,7 +25,7 @@ __global__ void colmean_kernel(const float* X, int layout, long ldx, int M, int 
 }
 
 // Eq. 1 as printed: the average column, i.e. the mean over columns of every row.
-__global__ void rowmean_kernel(const float* X, int layout, long ldx, int M, int N, double* mean) {
+static __global__ void rowmean_kernel(const float* X, int layout, long ldx, int M, int N, double* mean) {
     const int lane = threadIdx.x & 31;
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r >= M) return;
@@ -40,7 +40,7 @@ __global__ void rowmean_kernel(const float* X, int layout, long ldx, int M, int 
 // Each block writes the FP64 sum of squares of its tile to xpart.  Block
 // (0,0) also resets the fit kernel's barrier, abort flag and info words.
 // Tile: 32 columns x 32 panels (128 rows); 256 threads.
-__global__ void __launch_bounds__(kPackThreads) pack_kernel(const float* __restrict__ X, int layout, long ldx,
+static __global__ void __launch_bounds__(kPackThreads) pack_kernel(const float* __restrict__ X, int layout, long ldx,
                                                             int M, int N, int np, int center,
                                                             const double* __restrict__ cmean,
                                                             const double* __restrict__ rmean, float* R,
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const float* __restr
 // T (M x K, ld M), P (N x K, ld N), lambda, iters from the row-major
 // workspace factors.  Components >= found are zero.  mult: T = V * lambda_k
 // (GS) or T = V (NIPALS, V holds the unnormalised scores).
-__global__ void epilogue_kernel(const float* __restrict__ V, int ldv, const float* __restrict__ U, int ldu,
+static __global__ void epilogue_kernel(const float* __restrict__ V, int ldv, const float* __restrict__ U, int ldu,
                                 const double* __restrict__ lam_ws, const int* __restrict__ iters_ws,
                                 const int* __restrict__ info, int M, int N, int K, int gs, float* T, float* P,
                                 double* lambda, int* iters) {
@@ -153,7 +153,7 @@ __global__ void epilogue_kernel(const float* __restrict__ V, int ldv, const floa
 // R_out (M x N, ld M) from the panels; when every component was found the
 // deflation of the last one, R <- R - mult * V(K-1) U(K-1)^T (Eq. 3), is
 // applied here (inside the fit it happens in the next component's first pass).
-__global__ void __launch_bounds__(kPackThreads) unpack_kernel(const float* __restrict__ R, int M, int N, int np,
+static __global__ void __launch_bounds__(kPackThreads) unpack_kernel(const float* __restrict__ R, int M, int N, int np,
                                                               const float* __restrict__ V, int ldv,
                                                               const float* __restrict__ U, int ldu,
                                                               const double* __restrict__ lam_ws,
