@@ -5,23 +5,33 @@
 //   - a contiguous range of 4-row panels of R (rows [r0, r1)), and with them
 //     the same rows of V (score directions), vraw and vcorr;
 //   - a contiguous slice [n0, n1) of the N columns, and with it the same rows
-//     of U (loadings), W = R^T V, upre.
-// Only partial sums, the current loading `ut`, its FP32 copy `ucur` and a few
-// norms cross CTAs, always through a bounded grid barrier.
+//     of U (loadings), W = R^T V and upre.
+// Partial sums, the pass input `ut` and a few scalars cross CTAs, always
+// through a bounded grid barrier (device_common.cuh).
 //
-// One pass over R per power iteration.  A pass takes the normalised loading
-// u, forms v_raw = R u row panel by row panel (FP32 products, warp butterfly,
-// cross-warp sum) and, while the panel is still in registers, accumulates
-// s = R^T v_raw.  For GS-PCA the score correction v = (v_raw - V b)/lambda,
-// b = V^T v_raw, commutes through R^T: R^T v = (s - W b)/lambda with W = R^T V
-// kept up to date by a rank-1 update per component, so the paper's second
-// matrix-vector product (u = R^T v) needs no second read of R.  The rank-1
-// deflation of component k-1 (Eq. 3) is applied inside the first pass of
-// component k, which also extracts the start column R(k).
+// One pass over R per power iteration.  A pass takes the current loading up to
+// a positive factor nu (known exactly from the squared-norm partials of its
+// input), forms v' = R u' panel by panel (FP32 products, warp butterfly,
+// cross-warp sum) and, while the panel is still on chip, accumulates
+// s' = R^T v'.  For GS-PCA the score correction v' - V b', b' = V^T v',
+// commutes through R^T: R^T (v' - V b') = s' - W b' with W = R^T V kept up to
+// date by a rank-1 update per component, so the paper's second matrix-vector
+// product needs no second read of R.  The rank-1 deflation of component k-1
+// (Eq. 3) is applied inside the first pass of component k, which also takes
+// the start column R(k).  Panels reach shared memory through a ring of 1-D
+// TMA bulk copies; the first stages of every pass are issued before the
+// barrier that precedes it.
 //
-// Precision: R and every O(M k), O(N k) product are FP32 with FP32 sums
-// inside a CTA; sums across CTAs, the Gram-Schmidt coefficients' use against
-// FP64 vectors, every norm, lambda and the convergence test are FP64.
+// Barriers per iteration: NIPALS and GS component 0 need two (after the
+// pass; after the new loading); GS components k > 0 need three (one more
+// after u_pre' = s' - W b' and its coefficients a' = U^T u_pre').  The
+// k-vectors b' and a' are reduced by every CTA from the CTA partials when G*k
+// is small, otherwise once across the grid with one more barrier each.
+//
+// Precision: R and every O(M N), O(M k), O(N k) product are FP32 with FP32
+// sums inside a CTA; cross-CTA vector sums are FP32 over the CTA partials of
+// one lane combined in float-float across lanes; every norm and scalar sum
+// is float-float; lambda and the convergence test are FP64.
 #pragma once
 
 #include "device_common.cuh"
@@ -30,6 +40,7 @@ namespace gspca {
 
 constexpr int kBlock = 512;
 constexpr int kMaxWarps = kBlock / 32;
+constexpr int kMaxStages = 4;
 
 enum : int { kInfoStatus = 0, kInfoFound = 1, kInfoItersLo = 2, kInfoItersHi = 3, kInfoWords = 8 };
 
@@ -48,37 +59,68 @@ struct FitArgs {
     int ldu;
     float* W;                 // N x ldw row-major (R^T V)
     int ldw;
-    float* vraw;              // Mp
-    float* vcorr;             // Mp
-    float* ut;                // N, unnormalised current loading
-    double* upre;             // N
-    float* ucur;              // N, FP32 normalised loading used by the last pass
-    float* part;              // G x L vector partials
-    int L;
-    double* spart;            // G x 4 scalar partials
-    double* red;              // L reduced vectors
-    double* reds;             // 4 reduced scalars
-    double* normpart;         // G partial squared norms of ut
+    float* vraw;              // Mp: v' of the last pass
+    float* vcorr;             // Mp: v' - V b'
+    float* ut;                // 2 x N: pass input, double-buffered
+    float* upre;              // N: s' - W b' (pass scale)
+    float* partA;             // G x LA vector partials of the pass (s' | b' or Gram row)
+    int LA;
+    float* partB;             // G x LB vector partials of the GS step (a')
+    int LB;
+    float2* spart;            // G x 4 float-float scalars: [0] pass, [1] lambda'^2, [2+b] ||ut[b]||^2
+    double* red;              // LA doubles: grid-wide reductions (large k, start-column fallback)
     double* lam;              // K
     int* iters;               // K
     int* info;                // kInfoWords
-    unsigned* bar;            // [count, generation]
+    unsigned* flags;          // barrier arrival counter (flags[0]), zeroed before the launch
     int* abort;
     const int* iters_lock;    // device, K entries, nullable
     unsigned long long timeout_ns;
+    unsigned long long* timing;  // phase-time accumulators (instrumented builds only), nullable
+    int tma_stages;           // TMA ring stages (0 = panels loaded straight into registers)
+    int ldk;                  // shared-memory length of the k-vectors (>= K)
+    int max_slice;            // shared-memory length of the N slice (>= n1 - n0)
+    int redundant_max;        // reduce k-vectors in every CTA when k <= this
 };
 
 struct __align__(16) SmemFit {
     float wsum[kMaxWarps][32];
     float vrow[2][32];
     float tmpf[kMaxWarps][128];
-    double dtmp[kMaxWarps * 4];
-    double bcast[4];
+    ff ffw[kMaxWarps];
+    ff ffq[kMaxWarps][4];
+    ff sff[4];
+    ff lamff;
+    double dsc[4];
+    unsigned long long mbar[kMaxStages];
     int flag;
     int sel;
+    int stop;
+#ifdef GSPCA_PHASE_TIMING
+    unsigned long long tacc[16];
+    unsigned long long tlast;
+    int tcur;
+#endif
 };
 
-enum : int { kPassDot = 0, kPassCol = 1, kPassSq = 2 };
+// Instrumented builds (-DGSPCA_PHASE_TIMING) accumulate, in CTA 0, the
+// %globaltimer time spent in each phase of the loop; product builds compile
+// the marks away.
+#ifdef GSPCA_PHASE_TIMING
+#define PHASE_MARK(id)                                      \
+    do {                                                    \
+        if (blockIdx.x == 0 && threadIdx.x == 0) {          \
+            const unsigned long long t_ = globaltimer_ns(); \
+            sm.tacc[sm.tcur] += t_ - sm.tlast;              \
+            sm.tlast = t_;                                  \
+            sm.tcur = (id);                                 \
+        }                                                   \
+    } while (0)
+#else
+#define PHASE_MARK(id) \
+    do {               \
+    } while (0)
+#endif
 
 template <int CPT>
 struct PassShape {
@@ -86,37 +128,106 @@ struct PassShape {
     static constexpr int RPR = 4 * PPR;                   // rows per round
 };
 
+// ------------------------------------------------------------------ TMA ring
+
+// Per-CTA ring of S shared-memory stages, each holding PPR consecutive panels
+// of this CTA's rows.  Sequence numbers run across passes: sequence q lives in
+// stage q % S and completes phase (q / S) & 1 of that stage's mbarrier.  Only
+// thread 0 issues copies; every thread keeps the counters identically.
+struct Ring {
+    float* base;
+    unsigned long long* mbar;
+    int S;
+    int stage_floats;
+    unsigned issued;  // sequences issued so far
+    unsigned used;    // sequences consumed so far
+
+    __device__ __forceinline__ float* stage(unsigned q) const { return base + (size_t)(q % S) * stage_floats; }
+    __device__ __forceinline__ uint64_t* bar(unsigned q) const { return reinterpret_cast<uint64_t*>(&mbar[q % S]); }
+};
+
+// Issue round i (sequence rg.issued) of a pass over panels [p0, p1).
+__device__ __forceinline__ void ring_issue(const FitArgs& f, Ring& rg, int p0, int p1, int ppr, int i) {
+    const unsigned q = rg.issued;
+    const int pa = p0 + i * ppr;
+    const int npan = min(ppr, p1 - pa);
+    if (threadIdx.x == 0)
+        tma_load_1d(rg.stage(q), f.R + (size_t)pa * f.N * 4, (uint32_t)npan * (uint32_t)f.N * 16u, rg.bar(q));
+    rg.issued = q + 1;
+}
+
+// Issue the first rounds of the next pass (e.g. before the barrier preceding it).
+__device__ __forceinline__ void ring_prefetch(const FitArgs& f, Ring& rg, int p0, int p1, int ppr) {
+    if (rg.S == 0) return;
+    const int nrounds = (p1 - p0 + ppr - 1) / ppr;
+    for (int i = (int)(rg.issued - rg.used); i < rg.S && i < nrounds; ++i) ring_issue(f, rg, p0, p1, ppr, i);
+}
+
+// Before leaving the kernel early: wait (bounded) for the copies still in flight.
+__device__ __forceinline__ void ring_drain(const FitArgs& f, const Ring& rg) {
+    if (threadIdx.x == 0)
+        for (unsigned q = rg.used; q < rg.issued; ++q)
+            if (!mbar_wait(rg.bar(q), (q / rg.S) & 1u, f.timeout_ns)) break;
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ passes
+
+enum : int { kPassDot = 0, kPassCol = 1, kPassSq = 2 };
+
 // One streaming pass over the CTA's panels [p0, p1).
-//   kPassDot: rows = R u (u in uc[]), written to vraw; sacc = R^T rows; sc = sum rows^2.
+//   kPassDot: rows = R u' (u' in uc[]), written to vraw; sacc = R^T rows;
+//             sc = sum rows^2.  Panels come through the TMA ring when S > 0.
 //   kPassCol: rows = R(:, kcol) after the optional deflation
-//             R <- R - (lamf * V(:, kprev)) ucur^T (uc[] holds ucur); sacc = R^T rows;
-//             sc = ||R(:, kcol)||^2 over the CTA's rows.
+//             R <- R - (lamf * V(:, kprev)) uc^T; sacc = R^T rows;
+//             sc = ||R(:, kcol)||^2 over the CTA's rows.  Register path.
 //   kPassSq : sacc = column sums of squares (start-column fallback).
+// Returns false (in every thread) if a bounded wait on the ring timed out.
 template <int CPT, int MODE>
-__device__ __forceinline__ void row_pass(const FitArgs& f, SmemFit& sm, int p0, int p1,
-                                         const float (&uc)[CPT], int kcol, bool deflate, float lamf,
-                                         int kprev, float (&sacc)[CPT], double& sc) {
+__device__ __forceinline__ bool row_pass(const FitArgs& f, SmemFit& sm, Ring& rg, int p0, int p1,
+                                         const float (&uc)[CPT], int kcol, bool deflate, float lamf, int kprev,
+                                         float (&sacc)[CPT], ff& sc) {
     constexpr int PPR = PassShape<CPT>::PPR;
     constexpr int RPR = PassShape<CPT>::RPR;
     constexpr int SH = 5 - Log2<RPR>::value;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int T = blockDim.x, N = f.N;
+    const bool tma = (MODE == kPassDot) && rg.S > 0;
     int owner = -1;
     if (MODE == kPassCol && (kcol % T) == tid) owner = kcol / T;
 #pragma unroll
     for (int i = 0; i < CPT; ++i) sacc[i] = 0.f;
-    double my = 0.0;
+    ff my = ff_zero();
+    int ok = 1;
+    if (tma) ring_prefetch(f, rg, p0, p1, PPR);
+    const unsigned base = rg.used;
     int buf = 0;
-    for (int pb = p0; pb < p1; pb += PPR, buf ^= 1) {
+    int round = 0;
+    for (int pb = p0; pb < p1; pb += PPR, buf ^= 1, ++round) {
         float4 d[PPR][CPT];
+        if (tma) {
+            const unsigned q = base + (unsigned)round;
+            if (!mbar_wait(rg.bar(q), (q / rg.S) & 1u, f.timeout_ns)) ok = 0;
+            const float* st = rg.stage(q);
 #pragma unroll
-        for (int pp = 0; pp < PPR; ++pp) {
-            const int p = pb + pp;
+            for (int pp = 0; pp < PPR; ++pp) {
 #pragma unroll
-            for (int i = 0; i < CPT; ++i) {
-                const int c = tid + i * T;
-                d[pp][i] = (p < p1 && c < N) ? ld_stream4(f.R + ((size_t)p * N + c) * 4)
-                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int i = 0; i < CPT; ++i) {
+                    const int c = tid + i * T;
+                    d[pp][i] = (pb + pp < p1 && c < N) ? lds128(st + ((size_t)pp * N + c) * 4)
+                                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int pp = 0; pp < PPR; ++pp) {
+                const int p = pb + pp;
+#pragma unroll
+                for (int i = 0; i < CPT; ++i) {
+                    const int c = tid + i * T;
+                    d[pp][i] = (p < p1 && c < N) ? ld_stream4(f.R + ((size_t)p * N + c) * 4)
+                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
             }
         }
         if (MODE == kPassCol && deflate) {
@@ -160,12 +271,17 @@ __device__ __forceinline__ void row_pass(const FitArgs& f, SmemFit& sm, int p0, 
             const float r = warp_multi_reduce<RPR>(acc, lane);
             if ((lane & ((1 << SH) - 1)) == 0) sm.wsum[warp][lane >> SH] = r;
             __syncthreads();
+            // every thread has its panel data in registers: refill this stage
+            if (tma) {
+                const int ahead = round + rg.S;
+                if (pb + rg.S * PPR < p1 && (int)(rg.issued - base) == ahead) ring_issue(f, rg, p0, p1, PPR, ahead);
+            }
             if (tid < RPR) {
                 float s = 0.f;
                 for (int w = 0; w < nw; ++w) s += sm.wsum[w][tid];
                 if (pb + (tid >> 2) < p1) {
                     f.vraw[(size_t)pb * 4 + tid] = s;
-                    my += (double)s * (double)s;
+                    my = ff_add(my, ff_sqr(s));
                 }
                 sm.vrow[buf][tid] = s;
             }
@@ -184,7 +300,10 @@ __device__ __forceinline__ void row_pass(const FitArgs& f, SmemFit& sm, int p0, 
                     sm.vrow[buf][pp * 4 + 1] = x.y;
                     sm.vrow[buf][pp * 4 + 2] = x.z;
                     sm.vrow[buf][pp * 4 + 3] = x.w;
-                    my += (double)x.x * x.x + (double)x.y * x.y + (double)x.z * x.z + (double)x.w * x.w;
+                    my = ff_add(my, ff_sqr(x.x));
+                    my = ff_add(my, ff_sqr(x.y));
+                    my = ff_add(my, ff_sqr(x.z));
+                    my = ff_add(my, ff_sqr(x.w));
                 }
             }
             __syncthreads();
@@ -215,35 +334,53 @@ __device__ __forceinline__ void row_pass(const FitArgs& f, SmemFit& sm, int p0, 
                 }
         }
     }
+    if (tma) rg.used = base + (unsigned)round;
     // CTA total of `my` (nonzero only in warp 0 for kPassDot, in the owner for kPassCol).
     if (MODE == kPassDot) {
         if (warp == 0) {
-            const double t = warp_sum(my);
-            if (lane == 0) sm.bcast[0] = t;
+            const ff t = warp_sum_ff(my);
+            if (lane == 0) sm.sff[3] = t;
         }
     } else if (MODE == kPassCol) {
-        if (owner >= 0) sm.bcast[0] = my;
+        if (owner >= 0) sm.sff[3] = my;
     } else {
-        if (tid == 0) sm.bcast[0] = 0.0;
+        if (tid == 0) sm.sff[3] = ff_zero();
     }
+    const int all_ok = __syncthreads_and(ok);
+    sc = sm.sff[3];
     __syncthreads();
-    sc = sm.bcast[0];
-    __syncthreads();
+    return all_ok != 0;
 }
 
+// ------------------------------------------------------------------ small products
+
 // dst[j] = sum_{r in [r0, r1)} A[r*lda + j] * y(r) for j < kk, FP32 within the CTA.
+// A warp takes rows r0 + warp + 16 i (i < 8 per block) and issues every load
+// of the block (A and y) before using any of them.
 template <class Y>
-__device__ __forceinline__ void rows_times_matrix(const float* A, int lda, int r0, int r1, int kk, Y y,
-                                                  float* dst, SmemFit& sm) {
+__device__ __forceinline__ void rows_times_matrix(const float* A, int lda, int r0, int r1, int kk, Y y, float* dst,
+                                                  SmemFit& sm) {
+    constexpr int MAXR = 8;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     for (int j0 = 0; j0 < kk; j0 += 128) {
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int r = r0 + warp; r < r1; r += nw) {
-            const float yr = y(r);
-            const float* a = A + (size_t)r * lda + j0 + lane;
+        for (int rb = r0 + warp; rb < r1; rb += nw * MAXR) {
+            float a[MAXR][4], yr[MAXR];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (j0 + lane + 32 * q < kk) acc[q] = fmaf(ldcg(a + 32 * q), yr, acc[q]);
+            for (int i = 0; i < MAXR; ++i) {
+                const int r = rb + nw * i;
+                const bool ok = r < r1;
+                yr[i] = ok ? y(r) : 0.f;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int j = j0 + lane + 32 * q;
+                    a[i][q] = (ok && j < kk) ? ldcg(A + (size_t)r * lda + j) : 0.f;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < MAXR; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] = fmaf(a[i][q], yr[i], acc[q]);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) sm.tmpf[warp][lane + 32 * q] = acc[q];
@@ -257,180 +394,296 @@ __device__ __forceinline__ void rows_times_matrix(const float* A, int lda, int r
     }
 }
 
-// For r in [r0, r1): fn(r, sum_j A[r*lda + j] * x[j]) with x (kk floats) in shared memory.
-template <class Fn>
-__device__ __forceinline__ void matrix_times_vector(const float* A, int lda, int r0, int r1, int kk,
-                                                    const float* x, Fn fn) {
+// For every row r in [r0, r1): fn(r, sum_j A[r*lda + j] * x[j], pre(r)) with x
+// (kk floats) in shared memory; fn runs in one lane per row.  A warp takes rows
+// r0 + warp + 16 i (i < 8 per block), issues all their loads (and pre(r))
+// first, and reduces the 8 row sums across lanes with one multi-value
+// butterfly.
+template <class Pre, class Fn>
+__device__ __forceinline__ void matrix_times_vector(const float* A, int lda, int r0, int r1, int kk, const float* x,
+                                                    Pre pre, Fn fn) {
+    constexpr int MAXR = 8, MAXJ = 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int r = r0 + warp; r < r1; r += nw) {
-        float s = 0.f;
-        const float* a = A + (size_t)r * lda;
-        for (int j = lane; j < kk; j += 32) s = fmaf(ldcg(a + j), x[j], s);
-        s = warp_sum(s);
-        fn(r, s, lane);
-    }
-}
-
-// CTA-wide FP64 sum of per-thread values in a fixed order (deterministic).
-__device__ __forceinline__ double block_sum(double v, SmemFit& sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_sum(v);
-    if (lane == 0) sm.dtmp[warp] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += sm.dtmp[w];
-        sm.bcast[1] = s;
-    }
-    __syncthreads();
-    const double r = sm.bcast[1];
-    __syncthreads();
-    return r;
-}
-
-// Reduce the vector partials part[0..G)[0..Lc) into red[0..Lc): columns are
-// dealt out in groups of 4 to the warps of all CTAs in a fixed pattern; a
-// lane sums every 8th CTA row in FP32 and the 8 lanes of a column combine
-// in FP64 through a fixed butterfly.  If outv != nullptr, columns c < sq_n
-// are also stored to outv (FP32) and their squares summed into normpart[g].
-// CTA G-1 also reduces the nsc scalar partials spart[.][0..nsc) in FP64.
-__device__ __forceinline__ void slice_reduce(const FitArgs& f, int Lc, float* outv, int sq_n, int nsc,
-                                             SmemFit& sm) {
-    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int ng = (Lc + 3) >> 2;
-    const int g0 = (int)(((long long)g * ng) / G), g1 = (int)(((long long)(g + 1) * ng) / G);
-    double sq = 0.0;
-    for (int grp = g0 + warp; grp < g1; grp += nw) {
-        const int c = grp * 4 + (lane & 3);
-        float s = 0.f;
-        if (c < Lc)
-            for (int r = lane >> 2; r < G; r += 8) s += ldcg(f.part + (size_t)r * f.L + c);
-        double d = (double)s;
-        d += __shfl_xor_sync(kFull, d, 4);
-        d += __shfl_xor_sync(kFull, d, 8);
-        d += __shfl_xor_sync(kFull, d, 16);
-        if (lane < 4 && c < Lc) {
-            f.red[c] = d;
-            if (outv != nullptr && c < sq_n) {
-                outv[c] = (float)d;
-                sq += d * d;
+    for (int rb = r0 + warp; rb < r1; rb += nw * MAXR) {
+        float acc[MAXR], pv[MAXR];
+#pragma unroll
+        for (int i = 0; i < MAXR; ++i) {
+            acc[i] = 0.f;
+            const int r = rb + nw * i;
+            pv[i] = (r < r1) ? pre(r) : 0.f;
+        }
+        for (int j0 = 0; j0 < kk; j0 += 32 * MAXJ) {
+            float a[MAXR][MAXJ];
+#pragma unroll
+            for (int i = 0; i < MAXR; ++i)
+#pragma unroll
+                for (int q = 0; q < MAXJ; ++q) {
+                    const int r = rb + nw * i, j = j0 + lane + 32 * q;
+                    a[i][q] = (r < r1 && j < kk) ? ldcg(A + (size_t)r * lda + j) : 0.f;
+                }
+#pragma unroll
+            for (int q = 0; q < MAXJ; ++q) {
+                const int j = j0 + lane + 32 * q;
+                const float xj = j < kk ? x[j] : 0.f;
+#pragma unroll
+                for (int i = 0; i < MAXR; ++i) acc[i] = fmaf(a[i][q], xj, acc[i]);
             }
         }
-    }
-    if (outv != nullptr) {
-        if (lane < 4) sm.dtmp[warp * 4 + lane] = sq;
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int i = 0; i < nw * 4; ++i) t += sm.dtmp[i];
-            f.normpart[g] = t;
-        }
-        __syncthreads();
-    }
-    if (nsc > 0 && g == G - 1 && warp == nw - 1) {
-        for (int s = 0; s < nsc; ++s) {
-            double t = 0.0;
-            for (int r = lane; r < G; r += 32) t += ldcg(f.spart + (size_t)r * 4 + s);
-            t = warp_sum(t);
-            if (lane == 0) f.reds[s] = t;
-        }
+        const float sum = warp_multi_reduce<MAXR>(acc, lane);  // lane l: row index l >> 2
+        const int i = lane >> 2;
+        float p = pv[0];
+#pragma unroll
+        for (int t = 1; t < MAXR; ++t)
+            if (t == i) p = pv[t];
+        const int r = rb + nw * i;
+        if ((lane & 3) == 0 && r < r1) fn(r, sum, p);
     }
 }
 
-// Sum of the G norm partials, same order in every CTA.
-__device__ __forceinline__ double sum_normparts(const FitArgs& f, SmemFit& sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// CTA-wide float-float sum (deterministic: warp butterflies, then a 16-lane
+// butterfly over the warp sums), result in every thread.
+__device__ __forceinline__ ff block_sum_ff(ff v, SmemFit& sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum_ff(v);
+    if (lane == 0) sm.ffw[warp] = v;
+    __syncthreads();
     if (warp == 0) {
-        double t = 0.0;
-        for (int r = lane; r < (int)gridDim.x; r += 32) t += ldcg(f.normpart + r);
-        t = warp_sum(t);
-        if (lane == 0) sm.bcast[2] = t;
+        ff t = lane < nw ? sm.ffw[lane] : ff_zero();
+#pragma unroll
+        for (int o = 8; o >= 1; o >>= 1) t = ff_add(t, ff_shfl_xor(t, o));
+        if (lane == 0) sm.sff[2] = t;
     }
     __syncthreads();
-    const double r = sm.bcast[2];
+    const ff r = sm.sff[2];
     __syncthreads();
     return r;
 }
+
+// ------------------------------------------------------------------ reductions
+
+// Every CTA reduces, over the G CTA rows,
+//   - nq <= 2 float-float scalar slots s0, s1 into sm.sff[0..nq), and
+//   - nv virtual columns col(v) of a FP32 partial buffer into out[0..nv)
+//     (shared memory, FP32 rounded from float-float).
+// All loads of the scalars and of the first block of 64 columns are issued
+// before any of them is used (one L2 round trip).  Warp w loads rows w, w+16,
+// ...; lane l loads columns l and l+32 of a block; a thread sums its rows in
+// FP32, the 16 warp sums of a column combine in a fixed float-float butterfly.
+template <class Col>
+__device__ __forceinline__ void gather_reduce(const FitArgs& f, SmemFit& sm, int nq, int s0, int s1,
+                                              const float* part, int L, int nv, Col col, float* out) {
+    constexpr int MAXI = 10, MAXJ = 2, NW = kMaxWarps;
+    const int G = gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    float2 q0 = make_float2(0.f, 0.f), q1 = make_float2(0.f, 0.f);
+    if (t < G) {
+        if (nq > 0) q0 = ldcg(f.spart + (size_t)t * 4 + s0);
+        if (nq > 1) q1 = ldcg(f.spart + (size_t)t * 4 + s1);
+    }
+    for (int vb = 0; vb < nv || vb == 0; vb += 32 * MAXJ) {
+        float s[MAXJ];
+#pragma unroll
+        for (int j = 0; j < MAXJ; ++j) s[j] = 0.f;
+        for (int rb = 0; rb < G && vb < nv; rb += NW * MAXI) {
+            float x[MAXI][MAXJ];
+#pragma unroll
+            for (int i = 0; i < MAXI; ++i)
+#pragma unroll
+                for (int j = 0; j < MAXJ; ++j) {
+                    const int r = rb + warp + NW * i, v = vb + lane + 32 * j;
+                    x[i][j] = (r < G && v < nv) ? ldcg(part + (size_t)r * L + col(v)) : 0.f;
+                }
+#pragma unroll
+            for (int j = 0; j < MAXJ; ++j)
+#pragma unroll
+                for (int i = 0; i < MAXI; ++i) s[j] += x[i][j];
+        }
+#pragma unroll
+        for (int j = 0; j < MAXJ; ++j) sm.tmpf[warp][lane + 32 * j] = s[j];
+        if (vb == 0 && nq > 0) {
+            const ff a0 = warp_sum_ff(ff{q0.x, q0.y});
+            const ff a1 = warp_sum_ff(ff{q1.x, q1.y});
+            if (lane == 0) {
+                sm.ffq[warp][0] = a0;
+                sm.ffq[warp][1] = a1;
+            }
+        }
+        __syncthreads();
+        {  // warp w combines columns 4w..4w+3 of the block: lane = 8*c + h
+            const int c = 4 * warp + (lane >> 3), h = lane & 7;
+            ff a = ff_add(ff{sm.tmpf[h][c], 0.f}, ff{sm.tmpf[h + 8][c], 0.f});
+            a = ff_add(a, ff_shfl_xor(a, 1));
+            a = ff_add(a, ff_shfl_xor(a, 2));
+            a = ff_add(a, ff_shfl_xor(a, 4));
+            if (h == 0 && vb + c < nv) out[vb + c] = __fadd_rn(a.hi, a.lo);
+        }
+        if (vb == 0 && nq > 0 && warp == NW - 1) {  // lane = 16*q + w
+            const int q = lane >> 4, w = lane & 15;
+            ff a = (q < nq) ? sm.ffq[w][q] : ff_zero();
+#pragma unroll
+            for (int o = 8; o >= 1; o >>= 1) a = ff_add(a, ff_shfl_xor(a, o));
+            if (w == 0 && q < nq) sm.sff[q] = a;
+        }
+        __syncthreads();
+    }
+}
+
+// Sum of column c of a G x L FP32 partial buffer: lane l adds CTA rows
+// l, l+32, ... in FP32 (loads issued together), then a fixed float-float
+// butterfly across the 32 lanes.  Result in every lane.
+__device__ __forceinline__ ff column_sum(const float* part, int L, int c) {
+    const int G = gridDim.x, lane = threadIdx.x & 31;
+    float s = 0.f;
+#pragma unroll 8
+    for (int r = lane; r < G; r += 32) s += ldcg(part + (size_t)r * L + c);
+    return warp_sum_ff(ff{s, 0.f});
+}
+
+// Columns [c0, c0+nc) reduced once across the whole grid into red[0..nc)
+// (FP64): columns are dealt to the warps of all CTAs in a fixed pattern.
+__device__ __forceinline__ void reduce_cols_distributed(const float* part, int L, int c0, int nc, double* red) {
+    const int G = gridDim.x, g = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const int gw = g * nw + warp, nwt = G * nw;
+    for (int c = gw; c < nc; c += nwt) {
+        const ff t = column_sum(part, L, c0 + c);
+        if (lane == 0) red[c] = ff_to_double(t);
+    }
+}
+
+__device__ __forceinline__ void write_scalar(const FitArgs& f, int slot, ff v) {
+    if (threadIdx.x == 0) f.spart[(size_t)blockIdx.x * 4 + slot] = make_float2(v.hi, v.lo);
+}
+
+// ------------------------------------------------------------------ kernel
 
 template <int CPT>
 __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
+    constexpr int PPR = PassShape<CPT>::PPR;
     __shared__ SmemFit sm;
-    extern __shared__ float dyn_smem[];
-    float* bs = dyn_smem;           // b (or a) as FP32, up to max(ldv, ldu) entries
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5;
+    const int N = f.N, K = f.K;
     const int p0 = (int)(((long long)g * f.np) / G), p1 = (int)(((long long)(g + 1) * f.np) / G);
     const int r0 = min(p0 * 4, f.M), r1 = min(p1 * 4, f.M);
-    const int n0 = (int)(((long long)g * f.N) / G), n1 = (int)(((long long)(g + 1) * f.N) / G);
-    const GridBarrier bar{f.bar, f.bar + 1, f.abort, f.timeout_ns};
+    const int n0 = (int)(((long long)g * N) / G), n1 = (int)(((long long)(g + 1) * N) / G);
+    const GridBarrier bar{f.flags, f.abort, f.timeout_ns};
     const bool gs = (f.algo == 1);
-    const int N = f.N, K = f.K;
-    float* part_g = f.part + (size_t)g * f.L;
+    float* pA = f.partA + (size_t)g * f.LA;
+    float* pB = f.partB + (size_t)g * f.LB;
 
+    Ring rg;
+    rg.S = f.tma_stages;
+    rg.stage_floats = PPR * N * 4;
+    rg.base = reinterpret_cast<float*>(dyn_smem);
+    rg.mbar = sm.mbar;
+    rg.issued = rg.used = 0;
+    // reduced pass partials: this CTA's N-slice, then the k-vector (b' or the Gram row)
+    float* rb = reinterpret_cast<float*>(dyn_smem + (size_t)rg.S * rg.stage_floats * sizeof(float));
+    float* ka = rb + f.max_slice + f.ldk;
+    const int nc1 = n1 - n0;
+    float* sv = rb;
+    float* kb = rb + nc1;
+    auto slice_then_k = [&](int v) { return v < nc1 ? n0 + v : N + (v - nc1); };
+    auto ident = [](int v) { return v; };
+
+    if (tid == 0) {
+        for (int s = 0; s < rg.S; ++s) mbar_init(reinterpret_cast<uint64_t*>(&sm.mbar[s]), 1);
+        fence_mbar_init();
+    }
+#ifdef GSPCA_PHASE_TIMING
+    if (g == 0 && tid == 0) {
+        for (int i = 0; i < 16; ++i) sm.tacc[i] = 0;
+        sm.tlast = globaltimer_ns();
+        sm.tcur = 0;
+    }
+#endif
     // ||X||_F^2 from the pack kernel's partials (fixed order, every CTA).
     if (warp == 0) {
         double t = 0.0;
         for (int i = lane; i < f.nxpart; i += 32) t += f.xpart[i];
         t = warp_sum(t);
-        if (lane == 0) sm.bcast[3] = t;
+        if (lane == 0) sm.dsc[0] = t;
     }
     __syncthreads();
-    const double thresh = f.eps_thresh * sqrt(sm.bcast[3]);
+    const float threshf = (float)(f.eps_thresh * sqrt(sm.dsc[0]));
+    const float tolf = (float)f.tol;
 
+    unsigned epoch = 0;
     int status = kStOK, found = K;
     long long total = 0;
-    double lam_prev = 0.0;
+    double lam_prev = 0.0;  // lambda of the last finished component
+    float vinv_prev = 0.f;  // 1/||v' - V b'|| of its last pass (GS)
+    float inv_nu = 0.f;     // 1/||ut[buf]||
+    int buf = 0;
     float uc[CPT], sacc[CPT];
-    double sc = 0.0;
+    ff sc;
+    bool alive = true;
+
+#define GS_SYNC()                          \
+    do {                                   \
+        if (!bar.sync(epoch, &sm.flag)) {  \
+            alive = false;                 \
+            goto leave;                    \
+        }                                  \
+    } while (0)
 
     for (int k = 0; k < K && found == K; ++k) {
-        // ---------------- start pass: deflate component k-1, take column k
-        __syncthreads();  // finalize of k-1 (V, U rows of this CTA) before they are read
+        // ------------- start: deflate component k-1 inside the pass that takes R(k)
+        __syncthreads();
+        PHASE_MARK(0);
         const bool defl = k > 0;
         const float lamf = gs ? (float)lam_prev : 1.f;
 #pragma unroll
         for (int i = 0; i < CPT; ++i) {
             const int c = tid + i * T;
-            uc[i] = (defl && c < N) ? ldcg(f.ucur + c) : 0.f;
+            uc[i] = (defl && c < N) ? ldcg(f.ut + (size_t)buf * N + c) * inv_nu : 0.f;
         }
-        row_pass<CPT, kPassCol>(f, sm, p0, p1, uc, k, defl, lamf, k - 1, sacc, sc);
+        row_pass<CPT, kPassCol>(f, sm, rg, p0, p1, uc, k, defl, lamf, k - 1, sacc, sc);
 #pragma unroll
         for (int i = 0; i < CPT; ++i) {
             const int c = tid + i * T;
-            if (c < N) part_g[c] = sacc[i];
+            if (c < N) pA[c] = sacc[i];
         }
-        if (tid == 0) f.spart[(size_t)g * 4] = sc;
-        if (gs && k > 0)  // Gram row G[k-1][j] = V(k-1)^T V(j), j <= k-1
+        write_scalar(f, 0, sc);
+        if (gs && k > 0)  // Gram row (V^T v_{k-1})_j over this CTA's rows
             rows_times_matrix(f.V, f.ldv, r0, r1, k, [&](int r) { return f.V[(size_t)r * f.ldv + (k - 1)]; },
-                              part_g + N, sm);
-        if (!bar.sync(&sm.flag)) return;
-        slice_reduce(f, N + (gs ? k : 0), gs ? nullptr : f.ut, gs ? 0 : N, 1, sm);
-        if (!bar.sync(&sm.flag)) return;
+                              pA + N, sm);
+        if (defl) fence_proxy_async_global();
+        GS_SYNC();
 
-        if (ldcg(f.reds) == 0.0) {
-            // Zero start column: restart from the residual column of largest norm
-            // (lowest index on ties); every column zero => rank exhausted.
-            row_pass<CPT, kPassSq>(f, sm, p0, p1, uc, 0, false, 0.f, 0, sacc, sc);
+        const bool small_k = k <= f.redundant_max;  // k-vectors reduced by every CTA
+        const int nk0 = (gs && k > 0 && small_k) ? k : 0;
+        gather_reduce(f, sm, 1, 0, 0, f.partA, f.LA, nc1 + nk0, slice_then_k, rb);
+        if (sm.sff[0].hi == 0.f && sm.sff[0].lo == 0.f) {
+            // Zero start column: restart from the residual column of largest
+            // norm (lowest index on ties); every column zero => rank exhausted.
+            row_pass<CPT, kPassSq>(f, sm, rg, p0, p1, uc, 0, false, 0.f, 0, sacc, sc);
 #pragma unroll
             for (int i = 0; i < CPT; ++i) {
                 const int c = tid + i * T;
-                if (c < N) part_g[c] = sacc[i];
+                if (c < N) pA[c] = sacc[i];
             }
-            if (!bar.sync(&sm.flag)) return;
-            slice_reduce(f, N, nullptr, 0, 0, sm);
-            if (!bar.sync(&sm.flag)) return;
+            GS_SYNC();
+            reduce_cols_distributed(f.partA, f.LA, 0, N, f.red);
+            GS_SYNC();
             if (warp == 0) {
                 double best = 0.0;
                 int bi = N;
                 for (int c = lane; c < N; c += 32) {
                     const double v = ldcg(f.red + c);
-                    if (v > best) { best = v; bi = c; }
+                    if (v > best) {
+                        best = v;
+                        bi = c;
+                    }
                 }
                 for (int o = 16; o >= 1; o >>= 1) {
                     const double ob = __shfl_xor_sync(kFull, best, o);
                     const int oi = __shfl_xor_sync(kFull, bi, o);
-                    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                    if (ob > best || (ob == best && oi < bi)) {
+                        best = ob;
+                        bi = oi;
+                    }
                 }
                 if (lane == 0) sm.sel = (best > 0.0) ? bi : -1;
             }
@@ -442,185 +695,242 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
                 status = kStDegenerate;
                 break;
             }
-            row_pass<CPT, kPassCol>(f, sm, p0, p1, uc, kcol, false, 0.f, 0, sacc, sc);
+            row_pass<CPT, kPassCol>(f, sm, rg, p0, p1, uc, kcol, false, 0.f, 0, sacc, sc);
 #pragma unroll
             for (int i = 0; i < CPT; ++i) {
                 const int c = tid + i * T;
-                if (c < N) part_g[c] = sacc[i];
+                if (c < N) pA[c] = sacc[i];
             }
-            if (!bar.sync(&sm.flag)) return;
-            slice_reduce(f, N, gs ? nullptr : f.ut, gs ? 0 : N, 0, sm);
-            if (!bar.sync(&sm.flag)) return;
+            write_scalar(f, 0, sc);
+            GS_SYNC();
+            gather_reduce(f, sm, 1, 0, 0, f.partA, f.LA, nc1 + nk0, slice_then_k, rb);
         }
-
-        if (gs) {
-            // W <- R_k^T V: rank-1 update for the deflation of component k-1 plus
-            // the new column R_k^T v_{k-1} = upre/lambda - lambda u_{k-1} (v^T v).
-            if (k > 0) {
-                const double lp = lam_prev;
+        // ||x||^2 rescales the new loading so that its norm stays O(1).
+        const float xx_inv = __fdiv_rn(1.f, __fadd_rn(sm.sff[0].hi, sm.sff[0].lo));
+        const int nb = buf ^ 1;
+        ff nq = ff_zero();
+        if (gs && k > 0) {
+            // Gram row -> kb; then W <- R_k^T V for the deflation of component k-1:
+            // W(:, j) -= lambda u (v_{k-1}.v_j), new column R_{k-1}^T v_{k-1} - lambda u |v_{k-1}|^2
+            if (!small_k) {
+                reduce_cols_distributed(f.partA, f.LA, N, k, f.red);
+                GS_SYNC();
+                for (int j = tid; j < k; j += T) kb[j] = (float)ldcg(f.red + j);
+                __syncthreads();
+            }
+            {
+                const int km = k - 1;
+                const float lpf = (float)lam_prev;
                 for (int e = tid; e < (n1 - n0) * k; e += T) {
                     const int n = n0 + e / k, jj = e % k;
-                    const double un = (double)f.U[(size_t)n * f.ldu + (k - 1)];
-                    const double gj = ldcg(f.red + N + jj);
+                    const float un = f.U[(size_t)n * f.ldu + km];
                     float* w = f.W + (size_t)n * f.ldw + jj;
-                    if (jj < k - 1)
-                        *w = (float)((double)*w - lp * un * gj);
+                    if (jj < km)
+                        *w = fmaf(-lpf * un, kb[jj], *w);
                     else
-                        *w = (float)(f.upre[n] / lp - lp * un * gj);
+                        *w = (float)((double)f.upre[n] * (double)vinv_prev - lam_prev * (double)un * (double)kb[km]);
                 }
-                __syncthreads();
             }
-            for (int n = n0 + tid; n < n1; n += T) f.upre[n] = ldcg(f.red + n);
             __syncthreads();
-            if (k > 0) {
-                rows_times_matrix(f.U, f.ldu, n0, n1, k, [&](int n) { return (float)f.upre[n]; }, part_g, sm);
-                if (!bar.sync(&sm.flag)) return;
-                slice_reduce(f, k, nullptr, 0, 0, sm);
-                if (!bar.sync(&sm.flag)) return;
-                for (int j = tid; j < k; j += T) bs[j] = (float)ldcg(f.red + j);
+            // u_pre = s0; a = U_(k)^T u_pre; ut = (u_pre - U a) / ||x||^2
+            for (int n = n0 + tid; n < n1; n += T) f.upre[n] = sv[n - n0];
+            __syncthreads();
+            rows_times_matrix(f.U, f.ldu, n0, n1, k, [&](int n) { return sv[n - n0]; }, pB, sm);
+            GS_SYNC();
+            if (small_k) {
+                gather_reduce(f, sm, 0, 0, 0, f.partB, f.LB, k, ident, ka);
+            } else {
+                reduce_cols_distributed(f.partB, f.LB, 0, k, f.red);
+                GS_SYNC();
+                for (int j = tid; j < k; j += T) ka[j] = (float)ldcg(f.red + j);
                 __syncthreads();
             }
-            double nq = 0.0;
-            if (k > 0) {
-                matrix_times_vector(f.U, f.ldu, n0, n1, k, bs, [&](int n, float s, int ln) {
-                    if (ln == 0) {
-                        const double un = f.upre[n] - (double)s;
-                        f.ut[n] = (float)un;
-                        nq += un * un;
-                    }
+            matrix_times_vector(
+                f.U, f.ldu, n0, n1, k, ka, [&](int n) { return sv[n - n0]; },
+                [&](int n, float s, float p) {
+                    const float un = (p - s) * xx_inv;
+                    f.ut[(size_t)nb * N + n] = un;
+                    nq = ff_add(nq, ff_sqr(un));
                 });
-            } else {
-                for (int n = n0 + tid; n < n1; n += T) {
-                    const double un = f.upre[n];
-                    f.ut[n] = (float)un;
-                    nq += un * un;
-                }
+        } else {
+            for (int n = n0 + tid; n < n1; n += T) {
+                const float un = sv[n - n0] * xx_inv;
+                f.ut[(size_t)nb * N + n] = un;
+                nq = ff_add(nq, ff_sqr(un));
             }
-            nq = block_sum(nq, sm);
-            if (tid == 0) f.normpart[g] = nq;
-            if (!bar.sync(&sm.flag)) return;
         }
+        nq = block_sum_ff(nq, sm);
+        write_scalar(f, 2 + nb, nq);
+        buf = nb;
+        ring_prefetch(f, rg, p0, p1, PPR);
+        GS_SYNC();
 
-        // ---------------- power iterations
-        double mu = 0.0, lam = 0.0;
+        // ------------- power iterations
+        ff mu = ff_zero();
         int j = 0;
         for (;;) {
-            const double nrm2 = sum_normparts(f, sm);
-            if (!(nrm2 > 0.0)) {
-                found = k;
-                status = kStDegenerate;
-                break;
-            }
-            const float inv = (float)(1.0 / sqrt(nrm2));
+            PHASE_MARK(1);
 #pragma unroll
             for (int i = 0; i < CPT; ++i) {
                 const int c = tid + i * T;
-                uc[i] = (c < N) ? ldcg(f.ut + c) * inv : 0.f;
-                if (g == 0 && c < N) f.ucur[c] = uc[i];
+                uc[i] = (c < N) ? ldcg(f.ut + (size_t)buf * N + c) : 0.f;
             }
-            row_pass<CPT, kPassDot>(f, sm, p0, p1, uc, 0, false, 0.f, 0, sacc, sc);
+            PHASE_MARK(2);
+            if (!row_pass<CPT, kPassDot>(f, sm, rg, p0, p1, uc, 0, false, 0.f, 0, sacc, sc)) {
+                if (tid == 0) atomicCAS(f.abort, 0, kStTimeout);
+                alive = false;
+                goto leave;
+            }
 #pragma unroll
             for (int i = 0; i < CPT; ++i) {
                 const int c = tid + i * T;
-                if (c < N) part_g[c] = sacc[i];
+                if (c < N) pA[c] = sacc[i];
             }
-            if (tid == 0) f.spart[(size_t)g * 4] = sc;
-            if (gs && k > 0)  // b = V_(k)^T v_raw over the CTA's rows
-                rows_times_matrix(f.V, f.ldv, r0, r1, k, [&](int r) { return f.vraw[r]; }, part_g + N, sm);
-            if (!bar.sync(&sm.flag)) return;
-            slice_reduce(f, N + (gs ? k : 0), gs ? nullptr : f.ut, gs ? 0 : N, 1, sm);
-            if (!bar.sync(&sm.flag)) return;
+            write_scalar(f, 0, sc);
+            if (gs && k > 0)  // b' = V_(k)^T v' over this CTA's rows
+                rows_times_matrix(f.V, f.ldv, r0, r1, k, [&](int r) { return f.vraw[r]; }, pA + N, sm);
+            PHASE_MARK(3);
+            GS_SYNC();
+            PHASE_MARK(4);
             ++j;
             ++total;
-            if (!gs) {
-                lam = sqrt(ldcg(f.reds));
-            } else if (k == 0) {
-                lam = sqrt(ldcg(f.reds));
-                for (int r = r0 + tid; r < r1; r += T) f.vcorr[r] = f.vraw[r];
-                for (int n = n0 + tid; n < n1; n += T) f.upre[n] = ldcg(f.red + n);
-            } else {
-                // v = v_raw - V b (rows), upre = s - W b (slice), a = U^T upre (partials)
-                for (int jj = tid; jj < k; jj += T) bs[jj] = (float)ldcg(f.red + N + jj);
-                __syncthreads();
-                double l2 = 0.0;
-                matrix_times_vector(f.V, f.ldv, r0, r1, k, bs, [&](int r, float s, int ln) {
-                    if (ln == 0) {
-                        const double vc = (double)f.vraw[r] - (double)s;
-                        f.vcorr[r] = (float)vc;
-                        l2 += vc * vc;
-                    }
-                });
-                matrix_times_vector(f.W, f.ldw, n0, n1, k, bs, [&](int n, float s, int ln) {
-                    if (ln == 0) f.upre[n] = ldcg(f.red + n) - (double)s;
-                });
-                __syncthreads();
-                rows_times_matrix(f.U, f.ldu, n0, n1, k, [&](int n) { return (float)f.upre[n]; }, part_g, sm);
-                l2 = block_sum(l2, sm);
-                if (tid == 0) f.spart[(size_t)g * 4] = l2;
-                if (!bar.sync(&sm.flag)) return;
-                slice_reduce(f, k, nullptr, 0, 1, sm);
-                if (!bar.sync(&sm.flag)) return;
-                lam = sqrt(ldcg(f.reds));
-            }
-            if (!(lam > thresh)) {
+            const bool small_k = k <= f.redundant_max;
+            // sff[0] = ||u'||^2 (pass input), sff[1] = ||v'||^2; this CTA's slice of s' (+ b')
+            gather_reduce(f, sm, 2, 2 + buf, 0, f.partA, f.LA, nc1 + ((gs && k > 0 && small_k) ? k : 0),
+                          slice_then_k, rb);
+            const ff nu2 = sm.sff[0];
+            const ff nvp = sm.sff[1];
+            const float nu2f = __fadd_rn(nu2.hi, nu2.lo);
+            if (!(nu2f > 0.f)) {
                 found = k;
                 status = kStDegenerate;
                 break;
             }
-            bool stop;
-            if (f.iters_lock != nullptr) {
-                stop = j >= f.iters_lock[k];
+            inv_nu = __fdiv_rn(1.f, __fsqrt_rn(nu2f));
+            ff lam2p;  // ||v' - V b'||^2 in pass scale
+            const int nbuf = buf ^ 1;
+            if (!gs || k == 0) {
+                lam2p = nvp;
+                PHASE_MARK(6);
             } else {
-                stop = fabs(mu - lam) < f.tol * lam;
-                if (!stop && j >= f.max_iter) {
-                    stop = true;
-                    if (status == kStOK) status = kStNotConverged;
+                // b' -> kb; v_corr' = v' - V b' (rows); u_pre' = s' - W b' (slice);
+                // a' = U^T u_pre' (partials)
+                if (!small_k) {
+                    reduce_cols_distributed(f.partA, f.LA, N, k, f.red);
+                    GS_SYNC();
+                    for (int jj = tid; jj < k; jj += T) kb[jj] = (float)ldcg(f.red + jj);
+                    __syncthreads();
                 }
+                PHASE_MARK(6);
+                ff l2 = ff_zero();
+                matrix_times_vector(
+                    f.V, f.ldv, r0, r1, k, kb, [&](int r) { return ldcg(f.vraw + r); },
+                    [&](int r, float s, float p) {
+                        const float vc = p - s;
+                        f.vcorr[r] = vc;
+                        l2 = ff_add(l2, ff_sqr(vc));
+                    });
+                matrix_times_vector(
+                    f.W, f.ldw, n0, n1, k, kb, [&](int n) { return sv[n - n0]; },
+                    [&](int n, float s, float p) { f.upre[n] = p - s; });
+                __syncthreads();
+                rows_times_matrix(f.U, f.ldu, n0, n1, k, [&](int n) { return f.upre[n]; }, pB, sm);
+                l2 = block_sum_ff(l2, sm);
+                write_scalar(f, 1, l2);
+                PHASE_MARK(7);
+                GS_SYNC();
+                PHASE_MARK(8);
+                gather_reduce(f, sm, 1, 1, 0, f.partB, f.LB, small_k ? k : 0, ident, ka);
+                lam2p = sm.sff[0];
+                if (!small_k) {
+                    reduce_cols_distributed(f.partB, f.LB, 0, k, f.red);
+                    GS_SYNC();
+                    for (int jj = tid; jj < k; jj += T) ka[jj] = (float)ldcg(f.red + jj);
+                    __syncthreads();
+                }
+                PHASE_MARK(10);
             }
-            if (stop) {
-                // Finalize component k: V(k), U(k), lambda_k, iters_k.
-                if (gs) {
-                    const double il = 1.0 / lam;
-                    for (int r = r0 + tid; r < r1; r += T)
-                        f.V[(size_t)r * f.ldv + k] = (float)((double)f.vcorr[r] * il);
+            // Thread 0: lambda = sqrt(lam2p / nu2) in FP64 and the test; the other
+            // threads form the next loading speculatively meanwhile.
+            if (tid == 0) {
+                const ff lamff = ff_sqrt(ff_div(lam2p, nu2));
+                int stop;
+                if (!(lamff.hi > threshf)) {
+                    stop = 2;
+                } else if (f.iters_lock != nullptr) {
+                    stop = j >= f.iters_lock[k];
                 } else {
-                    for (int r = r0 + tid; r < r1; r += T) f.V[(size_t)r * f.ldv + k] = f.vraw[r];
+                    const ff d = ff_add(mu, ff_neg(lamff));
+                    stop = fabsf(__fadd_rn(d.hi, d.lo)) < __fmul_rn(tolf, lamff.hi);
+                    if (!stop && j >= f.max_iter) stop = 3;
                 }
-                for (int n = n0 + tid; n < n1; n += T) f.U[(size_t)n * f.ldu + k] = ldcg(f.ucur + n);
-                if (g == 0 && tid == 0) {
-                    f.lam[k] = lam;
-                    f.iters[k] = j;
+                sm.lamff = lamff;
+                sm.stop = stop;
+            }
+            const float l2f = __fadd_rn(lam2p.hi, lam2p.lo);
+            const float nscale = __fdiv_rn(__fsqrt_rn(nu2f), l2f);  // keeps ||ut|| ~ 1
+            ff nq2 = ff_zero();
+            if (!gs || k == 0) {
+                for (int n = n0 + tid; n < n1; n += T) {
+                    const float un = sv[n - n0] * nscale;
+                    f.ut[(size_t)nbuf * N + n] = un;
+                    nq2 = ff_add(nq2, ff_sqr(un));
+                    if (gs) f.upre[n] = sv[n - n0];
                 }
-                lam_prev = lam;
+            } else {
+                matrix_times_vector(
+                    f.U, f.ldu, n0, n1, k, ka, [&](int n) { return ldcg(f.upre + n); },
+                    [&](int n, float s, float p) {
+                        const float un = (p - s) * nscale;
+                        f.ut[(size_t)nbuf * N + n] = un;
+                        nq2 = ff_add(nq2, ff_sqr(un));
+                    });
+            }
+            nq2 = block_sum_ff(nq2, sm);  // its barriers also publish sm.stop / sm.lamff
+            const int stop = sm.stop;
+            const ff lamff = sm.lamff;
+            if (stop == 2) {
+                found = k;
+                status = kStDegenerate;
                 break;
             }
-            mu = lam;
-            if (gs) {
-                double nq = 0.0;
-                if (k > 0) {
-                    for (int jj = tid; jj < k; jj += T) bs[jj] = (float)ldcg(f.red + jj);
-                    __syncthreads();
-                    matrix_times_vector(f.U, f.ldu, n0, n1, k, bs, [&](int n, float s, int ln) {
-                        if (ln == 0) {
-                            const double un = f.upre[n] - (double)s;
-                            f.ut[n] = (float)un;
-                            nq += un * un;
-                        }
-                    });
+            if (stop) {
+                if (stop == 3 && status == kStOK) status = kStNotConverged;
+                // finalize component k: V(k), U(k), lambda_k, iters_k
+                const float vinv = __fdiv_rn(1.f, __fsqrt_rn(l2f));
+                if (gs) {
+                    const float* src = (k > 0) ? f.vcorr : f.vraw;
+                    for (int r = r0 + tid; r < r1; r += T) f.V[(size_t)r * f.ldv + k] = src[r] * vinv;
                 } else {
-                    for (int n = n0 + tid; n < n1; n += T) {
-                        const double un = f.upre[n];
-                        f.ut[n] = (float)un;
-                        nq += un * un;
-                    }
+                    for (int r = r0 + tid; r < r1; r += T) f.V[(size_t)r * f.ldv + k] = f.vraw[r] * inv_nu;
                 }
-                nq = block_sum(nq, sm);
-                if (tid == 0) f.normpart[g] = nq;
-                if (!bar.sync(&sm.flag)) return;
+                for (int n = n0 + tid; n < n1; n += T)
+                    f.U[(size_t)n * f.ldu + k] = ldcg(f.ut + (size_t)buf * N + n) * inv_nu;
+                lam_prev = ff_to_double(lamff);
+                if (g == 0 && tid == 0) {
+                    f.lam[k] = lam_prev;
+                    f.iters[k] = j;
+                }
+                vinv_prev = vinv;
+                break;
             }
+            mu = lamff;
+            write_scalar(f, 2 + nbuf, nq2);
+            buf = nbuf;
+            ring_prefetch(f, rg, p0, p1, PPR);
+            PHASE_MARK(11);
+            GS_SYNC();
         }
     }
-    if (g == 0 && tid == 0) {
+#undef GS_SYNC
+leave:
+    if (!alive) ring_drain(f, rg);
+#ifdef GSPCA_PHASE_TIMING
+    PHASE_MARK(15);
+    if (g == 0 && tid == 0 && f.timing)
+        for (int i = 0; i < 16; ++i) f.timing[i] = sm.tacc[i];
+#endif
+    if (alive && g == 0 && tid == 0) {
         f.info[kInfoStatus] = status;
         f.info[kInfoFound] = found;
         f.info[kInfoItersLo] = (int)(total & 0x7fffffff);

@@ -1,25 +1,25 @@
-// Host side of the C ABI declared in include/gspca.h: handle and workspace
-// management, argument checks, and the launch sequence of one fit
+// Host side of the C ABI declared in include/gspca.h: handles and their
+// workspace, argument checks, and the launch sequence of one fit
 //   [centring means] -> pack X into R panels -> persistent fit kernel
 //   -> epilogue (T, P, lambda, iters) -> [unpack R_out]
 // all enqueued on the caller's stream.
 #include <cuda_runtime.h>
 
-#include <cfloat>
-#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 
 #include "../../include/gspca.h"
-#include "fit_kernel.cuh"
-#include "prep_kernels.cuh"
+#include "launch_common.cuh"
 
 using namespace gspca;
 
 namespace {
 
 char g_cuda_err[256] = "no CUDA error";
+#ifdef GSPCA_PHASE_TIMING
+unsigned long long* g_timing_dev = nullptr;  // instrumented builds only
+#endif
 
 bool cuda_ok(cudaError_t e) {
     if (e == cudaSuccess) return true;
@@ -27,14 +27,10 @@ bool cuda_ok(cudaError_t e) {
     return false;
 }
 
-#define GS_CUDA(call)                                        \
-    do {                                                     \
-        if (!cuda_ok(call)) return GSPCA_ERR_CUDA;           \
+#define GS_CUDA(call)                              \
+    do {                                           \
+        if (!cuda_ok(call)) return GSPCA_ERR_CUDA; \
     } while (0)
-
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-constexpr int kMaxCols = 16 * kBlock;  // columns one CTA can hold (CPT <= 16)
 
 }  // namespace
 
@@ -44,21 +40,11 @@ struct gspca_handle {
     int max_K = 0;
     gspca_dtype dtype = GSPCA_F32;
     int num_sms = 0;
-    int ld = 0;      // row stride of V, U, W (>= max_K)
-    int L = 0;       // row stride of the vector partials
-    int Gmax = 0;    // CTAs the partial buffers hold
-    int xpart_cap = 0;
-    void* ws = nullptr;
-    size_t ws_bytes = 0;
-    float *R = nullptr, *V = nullptr, *U = nullptr, *W = nullptr;
-    float *vraw = nullptr, *vcorr = nullptr, *ut = nullptr, *ucur = nullptr, *part = nullptr;
-    double *upre = nullptr, *spart = nullptr, *red = nullptr, *reds = nullptr, *normpart = nullptr;
-    double *lam = nullptr, *xpart = nullptr, *cmean = nullptr, *rmean = nullptr;
-    int *iters = nullptr, *info = nullptr, *abort = nullptr, *lock = nullptr;
-    unsigned* bar = nullptr;
-    int* h_info = nullptr;  // pinned
+    void* ws_base = nullptr;
+    Workspace ws{};
+    int* h_info = nullptr;                     // pinned
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the persistent kernel
-    // host-buffer entry point staging (lazily allocated)
+    // host-buffer entry point staging (allocated on first use)
     void* stage = nullptr;
     float *sX = nullptr, *sT = nullptr, *sP = nullptr, *sR = nullptr;
     double* slam = nullptr;
@@ -67,25 +53,6 @@ struct gspca_handle {
 };
 
 namespace {
-
-template <int CPT>
-cudaError_t launch_fit(const FitArgs& a, int G, size_t dyn, cudaStream_t s) {
-    void* args[] = {const_cast<FitArgs*>(&a)};
-    return cudaLaunchCooperativeKernel((const void*)fit_kernel<CPT>, dim3(G), dim3(kBlock), args, dyn, s);
-}
-
-template <int CPT>
-int occupancy(size_t dyn) {
-    int bps = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fit_kernel<CPT>, kBlock, dyn) != cudaSuccess) return 0;
-    return bps;
-}
-
-int cpt_for(int N) {
-    int c = 1;
-    while (c * kBlock < N) c *= 2;
-    return c;
-}
 
 gspca_status check_fit_args(gspca_t h, const void* X, gspca_layout layout, long ldx, int M, int N, int K,
                             double tol, int max_iter, gspca_algo algo, const void* T, const void* P,
@@ -114,117 +81,31 @@ gspca_status check_fit_args(gspca_t h, const void* X, gspca_layout layout, long 
 }
 
 // Enqueue one fit on device buffers.  Does not synchronise.
-gspca_status enqueue_fit(gspca_t h, cudaStream_t s, const float* X, gspca_layout layout, long ldx, int M,
-                         int N, int K, double tol, int max_iter, gspca_algo algo, float* T, float* P,
-                         double* lambda, int* iters, float* R_out, const gspca_opts* opts) {
+gspca_status enqueue_fit(gspca_t h, cudaStream_t s, const float* X, gspca_layout layout, long ldx, int M, int N,
+                         int K, double tol, int max_iter, gspca_algo algo, float* T, float* P, double* lambda,
+                         int* iters, float* R_out, const gspca_opts* opts) {
     const int center = opts ? opts->center : 0;
     const double timeout = (opts && opts->timeout_s > 0) ? opts->timeout_s : 2.0;
     const int np = (M + 3) / 4;
-    int launches = 0;
-
-    if (center == 1) {
-        colmean_kernel<<<(N + 7) / 8, 256, 0, s>>>(X, (int)layout, ldx, M, N, h->cmean);
-        ++launches;
-    } else if (center == 2) {
-        rowmean_kernel<<<(M + 7) / 8, 256, 0, s>>>(X, (int)layout, ldx, M, N, h->rmean);
-        ++launches;
-    }
-    const dim3 pgrid((N + 31) / 32, (np + 31) / 32);
-    const int nxpart = (int)(pgrid.x * pgrid.y);
-    if (nxpart > h->xpart_cap) return GSPCA_ERR_NOT_SUPPORTED;
-    pack_kernel<<<pgrid, kPackThreads, 0, s>>>(X, (int)layout, ldx, M, N, np, center, h->cmean, h->rmean, h->R,
-                                               h->xpart, h->bar, h->abort, h->info, kInfoWords);
-    ++launches;
-    if (!cuda_ok(cudaGetLastError())) return GSPCA_ERR_CUDA;
-
+    const int nxpart = ((N + 31) / 32) * ((np + 31) / 32);
+    if (nxpart > h->ws.xcap) return GSPCA_ERR_NOT_SUPPORTED;
+    Plan plan{};
+    GS_CUDA(plan_fit(h->device, h->num_sms, h->ws.G, M, N, K, opts, &plan));
     const int* lock_dev = nullptr;
     if (opts && opts->iters_lock) {
-        GS_CUDA(cudaMemcpyAsync(h->lock, opts->iters_lock, sizeof(int) * K, cudaMemcpyHostToDevice, s));
-        lock_dev = h->lock;
+        GS_CUDA(cudaMemcpyAsync(h->ws.lock, opts->iters_lock, sizeof(int) * K, cudaMemcpyHostToDevice, s));
+        lock_dev = h->ws.lock;
     }
-
-    FitArgs a{};
-    a.M = M;
-    a.N = N;
-    a.K = K;
-    a.np = np;
-    a.algo = (int)algo;
-    a.max_iter = max_iter;
-    a.tol = tol;
-    a.eps_thresh = 64.0 * (double)FLT_EPSILON;
-    a.xpart = h->xpart;
-    a.nxpart = nxpart;
-    a.R = h->R;
-    a.V = h->V;
-    a.ldv = h->ld;
-    a.U = h->U;
-    a.ldu = h->ld;
-    a.W = h->W;
-    a.ldw = h->ld;
-    a.vraw = h->vraw;
-    a.vcorr = h->vcorr;
-    a.ut = h->ut;
-    a.upre = h->upre;
-    a.ucur = h->ucur;
-    a.part = h->part;
-    a.L = h->L;
-    a.spart = h->spart;
-    a.red = h->red;
-    a.reds = h->reds;
-    a.normpart = h->normpart;
-    a.lam = h->lam;
-    a.iters = h->iters;
-    a.info = h->info;
-    a.bar = h->bar;
-    a.abort = h->abort;
-    a.iters_lock = lock_dev;
-    a.timeout_ns = (unsigned long long)(timeout * 1e9);
-
-    const size_t dyn = sizeof(float) * (size_t)h->ld;
-    const int cpt = cpt_for(N);
-    int bps = 0;
-    switch (cpt) {
-        case 1: bps = occupancy<1>(dyn); break;
-        case 2: bps = occupancy<2>(dyn); break;
-        case 4: bps = occupancy<4>(dyn); break;
-        case 8: bps = occupancy<8>(dyn); break;
-        case 16: bps = occupancy<16>(dyn); break;
-        default: return GSPCA_ERR_NOT_SUPPORTED;
-    }
-    if (bps < 1) return GSPCA_ERR_CUDA;
-    const int rounds_ppr = (cpt >= 8) ? 1 : 8 / cpt;
-    int G = h->num_sms * bps;
-    const int want = (np + rounds_ppr - 1) / rounds_ppr;  // at least one full round per CTA
-    if (G > want) G = want;
-    if (opts && opts->grid_ctas > 0 && opts->grid_ctas < G) G = opts->grid_ctas;
-    if (G > h->Gmax) G = h->Gmax;
-    if (G < 1) G = 1;
-
-    if (!cuda_ok(cudaEventRecord(h->ev0, s))) return GSPCA_ERR_CUDA;
-    cudaError_t e = cudaSuccess;
-    switch (cpt) {
-        case 1: e = launch_fit<1>(a, G, dyn, s); break;
-        case 2: e = launch_fit<2>(a, G, dyn, s); break;
-        case 4: e = launch_fit<4>(a, G, dyn, s); break;
-        case 8: e = launch_fit<8>(a, G, dyn, s); break;
-        case 16: e = launch_fit<16>(a, G, dyn, s); break;
-    }
-    if (!cuda_ok(e)) return GSPCA_ERR_CUDA;
-    if (!cuda_ok(cudaEventRecord(h->ev1, s))) return GSPCA_ERR_CUDA;
-    ++launches;
-
-    const dim3 egrid((M + 31) / 32 + (N + 31) / 32, (K + 31) / 32);
-    epilogue_kernel<<<egrid, 256, 0, s>>>(h->V, h->ld, h->U, h->ld, h->lam, h->iters, h->info, M, N, K,
-                                          algo == GSPCA_GS, T, P, lambda, iters);
-    ++launches;
-    if (R_out) {
-        unpack_kernel<<<pgrid, kPackThreads, 0, s>>>(h->R, M, N, np, h->V, h->ld, h->U, h->ld, h->lam, h->info, K,
-                                                     algo == GSPCA_GS, R_out);
-        ++launches;
-    }
-    if (!cuda_ok(cudaGetLastError())) return GSPCA_ERR_CUDA;
-
-    h->last.grid_ctas = G;
+    FitArgs a = make_args(h->ws, plan, M, N, K, tol, max_iter, algo, lock_dev, timeout, nxpart);
+#ifdef GSPCA_PHASE_TIMING
+    if (!g_timing_dev) cudaMalloc(&g_timing_dev, 16 * sizeof(unsigned long long));
+    cudaMemsetAsync(g_timing_dev, 0, 16 * sizeof(unsigned long long), s);
+    a.timing = g_timing_dev;
+#endif
+    int launches = 0;
+    GS_CUDA(enqueue_sequence(h->ws, plan, a, s, X, layout, ldx, center, T, P, lambda, iters, R_out, h->ev0, h->ev1,
+                             &launches));
+    h->last.grid_ctas = plan.G;
     h->last.block_threads = kBlock;
     h->last.kernel_launches = launches;
     return GSPCA_OK;
@@ -232,8 +113,9 @@ gspca_status enqueue_fit(gspca_t h, cudaStream_t s, const float* X, gspca_layout
 
 // Algorithmic bytes of the persistent kernel for a finished fit: per pass one
 // read of R (M x N FP32); per component one extra write of R (the fused
-// deflation) ; GS-PCA reads V_(k) (M x k) and U_(k), W (N x k) each pass.
-double alg_bytes(int M, int N, int K, int found, const int* iters, bool gs) {
+// deflation); GS-PCA reads V_(k) twice (b', v') and U_(k) twice, W_(k) once
+// per iteration.
+double alg_bytes(int M, int N, int found, const int* iters, bool gs) {
     const double mn = (double)M * N * 4.0;
     double b = 0.0;
     for (int k = 0; k < found; ++k) {
@@ -245,19 +127,28 @@ double alg_bytes(int M, int N, int K, int found, const int* iters, bool gs) {
 }
 
 gspca_status finish(gspca_t h, cudaStream_t s, int K, gspca_algo algo, int M, int N) {
-    GS_CUDA(cudaMemcpyAsync(h->h_info, h->info, sizeof(int) * kInfoWords, cudaMemcpyDeviceToHost, s));
-    GS_CUDA(cudaMemcpyAsync(h->h_info + kInfoWords, h->abort, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaMemcpyAsync(h->h_info, h->ws.info, sizeof(int) * kInfoWords, cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaMemcpyAsync(h->h_info + kInfoWords, h->ws.abort, sizeof(int), cudaMemcpyDeviceToHost, s));
     int* hiters = h->h_info + kInfoWords + 4;
-    GS_CUDA(cudaMemcpyAsync(hiters, h->iters, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaMemcpyAsync(hiters, h->ws.iters, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
     GS_CUDA(cudaStreamSynchronize(s));
     float ms = 0.f;
     GS_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
     h->last.kernel_ms = ms;
     if (h->h_info[kInfoWords] != 0) return GSPCA_ERR_TIMEOUT;
+#ifdef GSPCA_PHASE_TIMING
+    {
+        unsigned long long t[16];
+        cudaMemcpy(t, g_timing_dev, sizeof(t), cudaMemcpyDeviceToHost);
+        std::fprintf(stderr, "PHASES");
+        for (int i = 0; i < 16; ++i) std::fprintf(stderr, " %llu", t[i]);
+        std::fprintf(stderr, "\n");
+    }
+#endif
     const int st = h->h_info[kInfoStatus];
     h->last.found = h->h_info[kInfoFound];
     h->last.total_iters = (long long)h->h_info[kInfoItersLo] + ((long long)h->h_info[kInfoItersHi] << 31);
-    h->last.alg_bytes = alg_bytes(M, N, K, h->last.found, hiters, algo == GSPCA_GS);
+    h->last.alg_bytes = alg_bytes(M, N, h->last.found, hiters, algo == GSPCA_GS);
     if (st == kStDegenerate) return GSPCA_ERR_DEGENERATE;
     if (st == kStNotConverged) return GSPCA_WARN_NOT_CONVERGED;
     return GSPCA_OK;
@@ -285,59 +176,18 @@ gspca_status gspca_create(gspca_t* out, int device, long max_M, long max_N, int 
         delete h;
         return GSPCA_ERR_CUDA;
     }
-    const long Mp = (max_M + 3) / 4 * 4;
-    h->ld = (int)align_up((size_t)max_K, 4);
-    h->L = (int)align_up((size_t)max_N + max_K + 4, 4);
-    h->Gmax = 4 * h->num_sms;
-    const long np = Mp / 4;
-    h->xpart_cap = (int)(((max_N + 31) / 32) * ((np + 31) / 32));
-
-    struct Item {
-        void** p;
-        size_t bytes;
-    } items[] = {
-        {(void**)&h->R, sizeof(float) * (size_t)Mp * max_N},
-        {(void**)&h->V, sizeof(float) * (size_t)Mp * h->ld},
-        {(void**)&h->U, sizeof(float) * (size_t)max_N * h->ld},
-        {(void**)&h->W, sizeof(float) * (size_t)max_N * h->ld},
-        {(void**)&h->vraw, sizeof(float) * (size_t)Mp},
-        {(void**)&h->vcorr, sizeof(float) * (size_t)Mp},
-        {(void**)&h->ut, sizeof(float) * (size_t)max_N},
-        {(void**)&h->ucur, sizeof(float) * (size_t)max_N},
-        {(void**)&h->upre, sizeof(double) * (size_t)max_N},
-        {(void**)&h->part, sizeof(float) * (size_t)h->Gmax * h->L},
-        {(void**)&h->spart, sizeof(double) * (size_t)h->Gmax * 4},
-        {(void**)&h->red, sizeof(double) * (size_t)h->L},
-        {(void**)&h->reds, sizeof(double) * 4},
-        {(void**)&h->normpart, sizeof(double) * (size_t)h->Gmax},
-        {(void**)&h->lam, sizeof(double) * (size_t)max_K},
-        {(void**)&h->xpart, sizeof(double) * (size_t)h->xpart_cap},
-        {(void**)&h->cmean, sizeof(double) * (size_t)max_N},
-        {(void**)&h->rmean, sizeof(double) * (size_t)Mp},
-        {(void**)&h->iters, sizeof(int) * (size_t)max_K},
-        {(void**)&h->info, sizeof(int) * kInfoWords},
-        {(void**)&h->abort, sizeof(int) * 4},
-        {(void**)&h->lock, sizeof(int) * (size_t)max_K},
-        {(void**)&h->bar, sizeof(unsigned) * 4},
-    };
-    size_t total = 0;
-    for (auto& it : items) total = align_up(total, 256) + align_up(it.bytes, 256);
+    const WsDims dims{(max_M + 3) / 4 * 4, (int)max_N, max_K, h->num_sms};
+    const Workspace probe = carve(nullptr, dims);
     void* base = nullptr;
-    cudaError_t e = cudaMalloc(&base, total);
+    cudaError_t e = cudaMalloc(&base, probe.bytes);
     if (e != cudaSuccess) {
         cuda_ok(e);
         delete h;
         return e == cudaErrorMemoryAllocation ? GSPCA_ERR_OOM : GSPCA_ERR_CUDA;
     }
-    h->ws = base;
-    h->ws_bytes = total;
-    size_t off = 0;
-    for (auto& it : items) {
-        off = align_up(off, 256);
-        *it.p = (char*)base + off;
-        off += align_up(it.bytes, 256);
-    }
-    if (!cuda_ok(cudaMemset(base, 0, total)) ||
+    h->ws_base = base;
+    h->ws = carve(base, dims);
+    if (!cuda_ok(cudaMemset(base, 0, probe.bytes)) ||
         !cuda_ok(cudaMallocHost((void**)&h->h_info, sizeof(int) * (kInfoWords + 4 + (size_t)max_K))) ||
         !cuda_ok(cudaEventCreate(&h->ev0)) || !cuda_ok(cudaEventCreate(&h->ev1))) {
         cudaFree(base);
@@ -392,7 +242,7 @@ gspca_status gspca_fit_host(gspca_t h, void* stream, const float* X, gspca_layou
     const size_t xbytes = layout == GSPCA_COL_MAJOR ? sizeof(float) * ((size_t)ldx * (N - 1) + M)
                                                     : sizeof(float) * ((size_t)ldx * (M - 1) + N);
     if (xbytes > sizeof(float) * (size_t)h->max_M * h->max_N) {
-        // a padded leading dimension larger than the staging buffer: pack rows/cols tightly
+        // a padded leading dimension larger than the staging buffer: copy tightly packed
         if (layout == GSPCA_COL_MAJOR)
             GS_CUDA(cudaMemcpy2DAsync(h->sX, sizeof(float) * M, X, sizeof(float) * ldx, sizeof(float) * M, N,
                                       cudaMemcpyHostToDevice, s));
@@ -434,7 +284,7 @@ gspca_status gspca_destroy(gspca_t h) {
     cudaSetDevice(h->device);
     gspca_status st = GSPCA_OK;
     if (h->stage && !cuda_ok(cudaFree(h->stage))) st = GSPCA_ERR_CUDA;
-    if (h->ws && !cuda_ok(cudaFree(h->ws))) st = GSPCA_ERR_CUDA;
+    if (h->ws_base && !cuda_ok(cudaFree(h->ws_base))) st = GSPCA_ERR_CUDA;
     if (h->h_info && !cuda_ok(cudaFreeHost(h->h_info))) st = GSPCA_ERR_CUDA;
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);

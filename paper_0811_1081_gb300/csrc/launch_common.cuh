@@ -1,0 +1,253 @@
+// Host-side helpers shared by the entry points: workspace layout, launch plan
+// (grid size, TMA ring depth, shared memory) and the enqueue sequence
+//   [centring means] -> pack -> persistent fit kernel -> epilogue [-> unpack]
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstddef>
+
+#include "../../include/gspca.h"
+#include "fit_kernel.cuh"
+#include "prep_kernels.cuh"
+
+namespace gspca {
+
+constexpr int kMaxCols = 16 * kBlock;   // columns one CTA holds (CPT <= 16)
+constexpr int kRedundantMax = 128;      // k up to which every CTA reduces a k-vector itself
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Dimensions the workspace is laid out for (maximum sizes for a handle, the
+// exact problem for the no-allocation entry point).
+struct WsDims {
+    long Mp;   // rows rounded up to a multiple of 4
+    int N, K;
+    int G;     // CTAs the partial buffers hold
+};
+
+inline int ws_ld(int K) { return (int)align_up((size_t)K, 4); }
+inline int ws_LA(int N, int K) { return (int)align_up((size_t)N + K + 4, 4); }
+inline int ws_xcap(long Mp, int N) { return (int)(((N + 31) / 32) * ((Mp / 4 + 31) / 32)); }
+
+struct Workspace {
+    float *R, *V, *U, *W, *vraw, *vcorr, *ut, *upre, *partA, *partB;
+    float2* spart;
+    double *red, *lam, *xpart, *cmean, *rmean;
+    int *iters, *info, *abort, *lock;
+    unsigned* flags;
+    int ld, LA, LB, G, xcap;
+    size_t bytes;
+};
+
+// Lay the workspace out from `base` (nullptr: only compute the size).
+inline Workspace carve(void* base, const WsDims& d) {
+    Workspace w{};
+    w.ld = ws_ld(d.K);
+    w.LA = ws_LA(d.N, d.K);
+    w.LB = w.ld;
+    w.G = d.G;
+    w.xcap = ws_xcap(d.Mp, d.N);
+    char* b = static_cast<char*>(base);
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void* {
+        off = align_up(off, 256);
+        void* p = b ? b + off : nullptr;
+        off += align_up(bytes > 0 ? bytes : 1, 256);
+        return p;
+    };
+    w.R = (float*)take(sizeof(float) * (size_t)d.Mp * d.N);
+    w.V = (float*)take(sizeof(float) * (size_t)d.Mp * w.ld);
+    w.U = (float*)take(sizeof(float) * (size_t)d.N * w.ld);
+    w.W = (float*)take(sizeof(float) * (size_t)d.N * w.ld);
+    w.vraw = (float*)take(sizeof(float) * (size_t)d.Mp);
+    w.vcorr = (float*)take(sizeof(float) * (size_t)d.Mp);
+    w.ut = (float*)take(sizeof(float) * 2 * (size_t)d.N);
+    w.upre = (float*)take(sizeof(float) * (size_t)d.N);
+    w.partA = (float*)take(sizeof(float) * (size_t)d.G * w.LA);
+    w.partB = (float*)take(sizeof(float) * (size_t)d.G * w.LB);
+    w.spart = (float2*)take(sizeof(float2) * 4 * (size_t)d.G);
+    w.red = (double*)take(sizeof(double) * (size_t)w.LA);
+    w.lam = (double*)take(sizeof(double) * (size_t)d.K);
+    w.xpart = (double*)take(sizeof(double) * (size_t)w.xcap);
+    w.cmean = (double*)take(sizeof(double) * (size_t)d.N);
+    w.rmean = (double*)take(sizeof(double) * (size_t)d.Mp);
+    w.iters = (int*)take(sizeof(int) * (size_t)d.K);
+    w.info = (int*)take(sizeof(int) * kInfoWords);
+    w.abort = (int*)take(sizeof(int) * 4);
+    w.lock = (int*)take(sizeof(int) * (size_t)d.K);
+    w.flags = (unsigned*)take(sizeof(unsigned) * 32);
+    w.bytes = off;
+    return w;
+}
+
+struct Plan {
+    int cpt, ppr, G, S, ldk, max_slice;
+    size_t dyn;
+};
+
+inline int cpt_for(int N) {
+    int c = 1;
+    while (c * kBlock < N) c *= 2;
+    return c;
+}
+
+template <int CPT>
+inline cudaError_t fit_attrs(size_t dyn, int* bps, int* static_smem) {
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, fit_kernel<CPT>);
+    if (e != cudaSuccess) return e;
+    *static_smem = (int)fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(fit_kernel<CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fit_kernel<CPT>, kBlock, dyn);
+}
+
+inline cudaError_t fit_attrs_any(int cpt, size_t dyn, int* bps, int* st) {
+    switch (cpt) {
+        case 1: return fit_attrs<1>(dyn, bps, st);
+        case 2: return fit_attrs<2>(dyn, bps, st);
+        case 4: return fit_attrs<4>(dyn, bps, st);
+        case 8: return fit_attrs<8>(dyn, bps, st);
+        default: return fit_attrs<16>(dyn, bps, st);
+    }
+}
+
+// Grid size, ring depth and shared memory for one problem.  Gcap bounds the
+// grid (the partial buffers' row count).
+inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int K, const gspca_opts* opts,
+                            Plan* p) {
+    p->cpt = cpt_for(N);
+    p->ppr = p->cpt >= 8 ? 1 : 8 / p->cpt;
+    const int np = (M + 3) / 4;
+    int G = num_sms;  // one CTA per SM (512 threads, >= 64 registers each)
+    const int want = (np + p->ppr - 1) / p->ppr;
+    if (G > want) G = want;
+    if (opts && opts->grid_ctas > 0 && opts->grid_ctas < G) G = opts->grid_ctas;
+    if (G > Gcap) G = Gcap;
+    if (G < 1) G = 1;
+    p->G = G;
+    p->ldk = ws_ld(K);
+    p->max_slice = (N + G - 1) / G + 1;
+    const size_t vec = sizeof(float) * (2 * (size_t)p->ldk + p->max_slice);
+    int optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e != cudaSuccess) return e;
+    int bps = 0, st = 0;
+    e = fit_attrs_any(p->cpt, vec, &bps, &st);
+    if (e != cudaSuccess) return e;
+    const size_t stage = (size_t)p->ppr * N * 16;
+    const long avail = (long)optin - st - (long)vec - 1024;
+    int S = avail > 0 ? (int)(avail / (long)stage) : 0;
+    if (S > kMaxStages) S = kMaxStages;
+    if (S < 2) S = 0;
+    p->S = S;
+    p->dyn = vec + (size_t)S * stage;
+    e = fit_attrs_any(p->cpt, p->dyn, &bps, &st);
+    if (e != cudaSuccess) return e;
+    if (bps < 1) return cudaErrorInvalidConfiguration;
+    return cudaSuccess;
+}
+
+template <int CPT>
+inline cudaError_t launch_fit_t(const FitArgs& a, const Plan& p, cudaStream_t s) {
+    void* args[] = {const_cast<FitArgs*>(&a)};
+    return cudaLaunchCooperativeKernel((const void*)fit_kernel<CPT>, dim3(p.G), dim3(kBlock), args, p.dyn, s);
+}
+
+inline cudaError_t launch_fit(const FitArgs& a, const Plan& p, cudaStream_t s) {
+    switch (p.cpt) {
+        case 1: return launch_fit_t<1>(a, p, s);
+        case 2: return launch_fit_t<2>(a, p, s);
+        case 4: return launch_fit_t<4>(a, p, s);
+        case 8: return launch_fit_t<8>(a, p, s);
+        default: return launch_fit_t<16>(a, p, s);
+    }
+}
+
+// FitArgs for a problem on a carved workspace.
+inline FitArgs make_args(const Workspace& w, const Plan& p, int M, int N, int K, double tol, int max_iter,
+                         gspca_algo algo, const int* lock_dev, double timeout_s, int nxpart) {
+    FitArgs a{};
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.np = (M + 3) / 4;
+    a.algo = (int)algo;
+    a.max_iter = max_iter;
+    a.tol = tol;
+    a.eps_thresh = 64.0 * (double)FLT_EPSILON;
+    a.xpart = w.xpart;
+    a.nxpart = nxpart;
+    a.R = w.R;
+    a.V = w.V;
+    a.ldv = w.ld;
+    a.U = w.U;
+    a.ldu = w.ld;
+    a.W = w.W;
+    a.ldw = w.ld;
+    a.vraw = w.vraw;
+    a.vcorr = w.vcorr;
+    a.ut = w.ut;
+    a.upre = w.upre;
+    a.partA = w.partA;
+    a.LA = w.LA;
+    a.partB = w.partB;
+    a.LB = w.LB;
+    a.spart = w.spart;
+    a.red = w.red;
+    a.lam = w.lam;
+    a.iters = w.iters;
+    a.info = w.info;
+    a.flags = w.flags;
+    a.abort = w.abort;
+    a.iters_lock = lock_dev;
+    a.timeout_ns = (unsigned long long)(timeout_s * 1e9);
+    a.timing = nullptr;
+    a.tma_stages = p.S;
+    a.ldk = p.ldk;
+    a.max_slice = p.max_slice;
+    a.redundant_max = kRedundantMax;
+    return a;
+}
+
+// Enqueue the launch sequence of one fit on `s` (no synchronisation).
+// Returns the number of kernels enqueued through *launches.
+inline cudaError_t enqueue_sequence(const Workspace& w, const Plan& p, FitArgs a, cudaStream_t s, const float* X,
+                                    gspca_layout layout, long ldx, int center, float* T, float* P,
+                                    double* lambda, int* iters, float* R_out, cudaEvent_t ev0, cudaEvent_t ev1,
+                                    int* launches) {
+    const int M = a.M, N = a.N, K = a.K, np = a.np;
+    int n = 0;
+    if (center == 1) {
+        colmean_kernel<<<(N + 7) / 8, 256, 0, s>>>(X, (int)layout, ldx, M, N, w.cmean);
+        ++n;
+    } else if (center == 2) {
+        rowmean_kernel<<<(M + 7) / 8, 256, 0, s>>>(X, (int)layout, ldx, M, N, w.rmean);
+        ++n;
+    }
+    const dim3 pgrid((N + 31) / 32, (np + 31) / 32);
+    pack_kernel<<<pgrid, kPackThreads, 0, s>>>(X, (int)layout, ldx, M, N, np, center, w.cmean, w.rmean, w.R,
+                                               w.xpart, w.flags, 1, w.abort, w.info, kInfoWords);
+    ++n;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return e;
+    if ((e = launch_fit(a, p, s)) != cudaSuccess) return e;
+    ++n;
+    if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return e;
+    const dim3 egrid((M + 31) / 32 + (N + 31) / 32, (K + 31) / 32);
+    epilogue_kernel<<<egrid, 256, 0, s>>>(w.V, w.ld, w.U, w.ld, w.lam, w.iters, w.info, M, N, K,
+                                          a.algo == GSPCA_GS, T, P, lambda, iters);
+    ++n;
+    if (R_out) {
+        unpack_kernel<<<pgrid, kPackThreads, 0, s>>>(w.R, M, N, np, w.V, w.ld, w.U, w.ld, w.lam, w.info, K,
+                                                     a.algo == GSPCA_GS, R_out);
+        ++n;
+    }
+    *launches = n;
+    return cudaGetLastError();
+}
+
+}  // namespace gspca

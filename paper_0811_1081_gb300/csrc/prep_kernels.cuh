@@ -38,21 +38,22 @@ static __global__ void rowmean_kernel(const float* X, int layout, long ldx, int 
 // Pack X (M x N, either layout) into R (4-row panels, padded rows zero), with
 // optional subtraction of column means (center 1) or row means (center 2).
 // Each block writes the FP64 sum of squares of its tile to xpart.  Block
-// (0,0) also resets the fit kernel's barrier, abort flag and info words.
+// (0,0) also clears the fit kernel's barrier words (one every 32), abort flag
+// and info words: everything the fit needs to start at zero.
 // Tile: 32 columns x 32 panels (128 rows); 256 threads.
 static __global__ void __launch_bounds__(kPackThreads) pack_kernel(const float* __restrict__ X, int layout, long ldx,
                                                             int M, int N, int np, int center,
                                                             const double* __restrict__ cmean,
                                                             const double* __restrict__ rmean, float* R,
-                                                            double* xpart, unsigned* bar, int* abort,
+                                                            double* xpart, unsigned* flags, int nflags, int* abort,
                                                             int* info, int ninfo) {
     __shared__ float tile[32][129];
     __shared__ double wsum[kPackThreads / 32];
     const int t = threadIdx.x;
     const int c0 = blockIdx.x * 32, p0 = blockIdx.y * 32, rbase = p0 * 4;
     if (blockIdx.x == 0 && blockIdx.y == 0) {
-        if (t < 2) bar[t] = 0u;
-        if (t == 2) *abort = 0;
+        for (int i = t; i < nflags; i += kPackThreads) flags[(size_t)i * 32] = 0u;
+        if (t == 0) *abort = 0;
         if (t < ninfo) info[t] = 0;
     }
     float sq = 0.f;
