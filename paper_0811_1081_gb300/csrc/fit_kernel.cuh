@@ -40,7 +40,7 @@ namespace gspca {
 
 constexpr int kBlock = 512;
 constexpr int kMaxWarps = kBlock / 32;
-constexpr int kMaxStages = 4;
+constexpr int kMaxStages = 8;
 
 enum : int { kInfoStatus = 0, kInfoFound = 1, kInfoItersLo = 2, kInfoItersHi = 3, kInfoWords = 8 };
 
@@ -78,13 +78,16 @@ struct FitArgs {
     unsigned long long timeout_ns;
     unsigned long long* timing;  // phase-time accumulators (instrumented builds only), nullable
     int tma_stages;           // TMA ring stages (0 = panels loaded straight into registers)
+    int dot_groups;           // 2: the loading pass runs as two independent 256-thread groups
     int ldk;                  // shared-memory length of the k-vectors (>= K)
     int max_slice;            // shared-memory length of the N slice (>= n1 - n0)
     int redundant_max;        // reduce k-vectors in every CTA when k <= this
 };
 
 struct __align__(16) SmemFit {
-    float wsum[kMaxWarps][32];
+    float wsum[2][kMaxWarps][32];
+    float wsum2[2][2][kMaxWarps / 2][4];
+    ff ffg[2];
     float vrow[2][32];
     float tmpf[kMaxWarps][128];
     ff ffw[kMaxWarps];
@@ -269,25 +272,24 @@ __device__ __forceinline__ bool row_pass(const FitArgs& f, SmemFit& sm, Ring& rg
                 }
             }
             const float r = warp_multi_reduce<RPR>(acc, lane);
-            if ((lane & ((1 << SH) - 1)) == 0) sm.wsum[warp][lane >> SH] = r;
+            if ((lane & ((1 << SH) - 1)) == 0) sm.wsum[buf][warp][lane >> SH] = r;
+            // One CTA barrier per round: the warp partials are double-buffered by
+            // round parity, and every warp finishes the row sums itself.
             __syncthreads();
             // every thread has its panel data in registers: refill this stage
             if (tma) {
                 const int ahead = round + rg.S;
                 if (pb + rg.S * PPR < p1 && (int)(rg.issued - base) == ahead) ring_issue(f, rg, p0, p1, PPR, ahead);
             }
-            if (tid < RPR) {
-                float s = 0.f;
-                for (int w = 0; w < nw; ++w) s += sm.wsum[w][tid];
-                if (pb + (tid >> 2) < p1) {
-                    f.vraw[(size_t)pb * 4 + tid] = s;
-                    my = ff_add(my, ff_sqr(s));
-                }
-                sm.vrow[buf][tid] = s;
+            float rs = 0.f;
+            if (lane < RPR)
+                for (int w = 0; w < nw; ++w) rs += sm.wsum[buf][w][lane];
+            if (warp == 0 && lane < RPR && pb + (lane >> 2) < p1) {
+                f.vraw[(size_t)pb * 4 + lane] = rs;
+                my = ff_add(my, ff_sqr(rs));
             }
-            __syncthreads();
 #pragma unroll
-            for (int r2 = 0; r2 < RPR; ++r2) rowv[r2] = sm.vrow[buf][r2];
+            for (int r2 = 0; r2 < RPR; ++r2) rowv[r2] = __shfl_sync(kFull, rs, r2);
         } else if (MODE == kPassCol) {
             if (owner >= 0) {
 #pragma unroll
@@ -348,6 +350,107 @@ __device__ __forceinline__ bool row_pass(const FitArgs& f, SmemFit& sm, Ring& rg
     }
     const int all_ok = __syncthreads_and(ok);
     sc = sm.sff[3];
+    __syncthreads();
+    return all_ok != 0;
+}
+
+__device__ __forceinline__ void named_barrier(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Loading pass (kPassDot) as two independent groups of 256 threads.  Group g
+// takes rounds g, g+2, ... of one 4-row panel each; its barriers are named
+// barriers of 256 threads, so while one group waits in its barrier or its
+// shuffle chain the other one computes.  Thread t of a group holds columns
+// t + 256 i (i < 2 CPT) of u' (uc2) and of its s' accumulators (sacc2).  The
+// ring holds one panel per stage and has an even number of stages, so round
+// r + S belongs to the same group as round r and that group refills its own
+// stages.  On return group 0 holds the CTA's s' partials and sc = sum v'^2.
+// Returns false (in every thread) if a bounded wait on the ring timed out.
+template <int CPT>
+__device__ __forceinline__ bool pass_dot2(const FitArgs& f, SmemFit& sm, Ring& rg, int p0, int p1,
+                                          const float (&uc2)[2 * CPT], float (&sacc2)[2 * CPT], ff& sc) {
+    constexpr int C2 = 2 * CPT;
+    const int tid = threadIdx.x, grp = tid >> 8, lt = tid & 255, lane = tid & 31, lw = (tid >> 5) & 7;
+    const int N = f.N;
+#pragma unroll
+    for (int i = 0; i < C2; ++i) sacc2[i] = 0.f;
+    ff my = ff_zero();
+    int ok = 1;
+    ring_prefetch(f, rg, p0, p1, 1);
+    const unsigned base = rg.used;
+    const int nrounds = p1 - p0;
+    for (int round = grp; round < nrounds; round += 2) {
+        const int p = p0 + round;
+        const unsigned q = base + (unsigned)round;
+        if (!mbar_wait(rg.bar(q), (q / rg.S) & 1u, f.timeout_ns)) ok = 0;
+        const float* st = rg.stage(q);
+        float4 d[C2];
+#pragma unroll
+        for (int i = 0; i < C2; ++i) {
+            const int c = lt + i * 256;
+            d[i] = c < N ? lds128(st + (size_t)c * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < C2; ++i) {
+            acc[0] = fmaf(d[i].x, uc2[i], acc[0]);
+            acc[1] = fmaf(d[i].y, uc2[i], acc[1]);
+            acc[2] = fmaf(d[i].z, uc2[i], acc[2]);
+            acc[3] = fmaf(d[i].w, uc2[i], acc[3]);
+        }
+        const float r = warp_multi_reduce<4>(acc, lane);  // lane l: row l >> 3
+        const int par = (round >> 1) & 1;
+        if ((lane & 7) == 0) sm.wsum2[grp][par][lw][lane >> 3] = r;
+        named_barrier(1 + grp, 256);
+        // this group has read the stage: refill it with round + S (same group)
+        if (lt == 0 && round + rg.S < nrounds)
+            tma_load_1d(rg.stage(q + rg.S), f.R + (size_t)(p + rg.S) * N * 4, (uint32_t)N * 16u, rg.bar(q + rg.S));
+        float rs = 0.f;
+        if (lane < 4)
+#pragma unroll
+            for (int w = 0; w < 8; ++w) rs += sm.wsum2[grp][par][w][lane];
+        if (lw == 0 && lane < 4 && 4 * p + lane < 4 * p1) {
+            f.vraw[(size_t)p * 4 + lane] = rs;
+            my = ff_add(my, ff_sqr(rs));
+        }
+        float rowv[4];
+#pragma unroll
+        for (int r2 = 0; r2 < 4; ++r2) rowv[r2] = __shfl_sync(kFull, rs, r2);
+#pragma unroll
+        for (int i = 0; i < C2; ++i) {
+            sacc2[i] = fmaf(d[i].x, rowv[0], sacc2[i]);
+            sacc2[i] = fmaf(d[i].y, rowv[1], sacc2[i]);
+            sacc2[i] = fmaf(d[i].z, rowv[2], sacc2[i]);
+            sacc2[i] = fmaf(d[i].w, rowv[3], sacc2[i]);
+        }
+    }
+    rg.used = base + (unsigned)nrounds;
+    rg.issued = rg.used;
+    if (lw == 0) {
+        const ff t = warp_sum_ff(my);
+        if (lane == 0) sm.ffg[grp] = t;
+    }
+    // group 1 hands its s' partials to group 0 through the (now idle) ring memory
+    const int all_ok = __syncthreads_and(ok);
+    float* xch = rg.base;
+    if (grp == 1)
+#pragma unroll
+        for (int i = 0; i < C2; ++i) {
+            const int c = lt + i * 256;
+            if (c < N) xch[c] = sacc2[i];
+        }
+    __syncthreads();
+    if (grp == 0)
+#pragma unroll
+        for (int i = 0; i < C2; ++i) {
+            const int c = lt + i * 256;
+            if (c < N) sacc2[i] += xch[c];
+        }
+    sc = ff_add(sm.ffg[0], sm.ffg[1]);
+    // the exchange area is ring memory: order these generic accesses before the
+    // next TMA writes into it
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     return all_ok != 0;
 }
@@ -574,7 +677,9 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
 
     Ring rg;
     rg.S = f.tma_stages;
-    rg.stage_floats = PPR * N * 4;
+    const bool two = f.dot_groups == 2;
+    const int ring_ppr = two ? 1 : PPR;
+    rg.stage_floats = ring_ppr * N * 4;
     rg.base = reinterpret_cast<float*>(dyn_smem);
     rg.mbar = sm.mbar;
     rg.issued = rg.used = 0;
@@ -762,7 +867,7 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
         nq = block_sum_ff(nq, sm);
         write_scalar(f, 2 + nb, nq);
         buf = nb;
-        ring_prefetch(f, rg, p0, p1, PPR);
+        ring_prefetch(f, rg, p0, p1, ring_ppr);
         GS_SYNC();
 
         // ------------- power iterations
@@ -770,21 +875,44 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
         int j = 0;
         for (;;) {
             PHASE_MARK(1);
+            bool pass_ok = true, two_done = false;
+            if constexpr (CPT <= 4) {
+                if (two) {
+                    float uc2[2 * CPT], sacc2[2 * CPT];
 #pragma unroll
-            for (int i = 0; i < CPT; ++i) {
-                const int c = tid + i * T;
-                uc[i] = (c < N) ? ldcg(f.ut + (size_t)buf * N + c) : 0.f;
+                    for (int i = 0; i < 2 * CPT; ++i) {
+                        const int c = (tid & 255) + i * 256;
+                        uc2[i] = (c < N) ? ldcg(f.ut + (size_t)buf * N + c) : 0.f;
+                    }
+                    PHASE_MARK(2);
+                    pass_ok = pass_dot2<CPT>(f, sm, rg, p0, p1, uc2, sacc2, sc);
+                    if (tid < 256)
+#pragma unroll
+                        for (int i = 0; i < 2 * CPT; ++i) {
+                            const int c = tid + i * 256;
+                            if (c < N) pA[c] = sacc2[i];
+                        }
+                    two_done = true;
+                }
             }
-            PHASE_MARK(2);
-            if (!row_pass<CPT, kPassDot>(f, sm, rg, p0, p1, uc, 0, false, 0.f, 0, sacc, sc)) {
+            if (!two_done) {
+#pragma unroll
+                for (int i = 0; i < CPT; ++i) {
+                    const int c = tid + i * T;
+                    uc[i] = (c < N) ? ldcg(f.ut + (size_t)buf * N + c) : 0.f;
+                }
+                PHASE_MARK(2);
+                pass_ok = row_pass<CPT, kPassDot>(f, sm, rg, p0, p1, uc, 0, false, 0.f, 0, sacc, sc);
+#pragma unroll
+                for (int i = 0; i < CPT; ++i) {
+                    const int c = tid + i * T;
+                    if (c < N) pA[c] = sacc[i];
+                }
+            }
+            if (!pass_ok) {
                 if (tid == 0) atomicCAS(f.abort, 0, kStTimeout);
                 alive = false;
                 goto leave;
-            }
-#pragma unroll
-            for (int i = 0; i < CPT; ++i) {
-                const int c = tid + i * T;
-                if (c < N) pA[c] = sacc[i];
             }
             write_scalar(f, 0, sc);
             if (gs && k > 0)  // b' = V_(k)^T v' over this CTA's rows
@@ -917,7 +1045,7 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
             mu = lamff;
             write_scalar(f, 2 + nbuf, nq2);
             buf = nbuf;
-            ring_prefetch(f, rg, p0, p1, PPR);
+            ring_prefetch(f, rg, p0, p1, ring_ppr);
             PHASE_MARK(11);
             GS_SYNC();
         }

@@ -83,7 +83,7 @@ inline Workspace carve(void* base, const WsDims& d) {
 }
 
 struct Plan {
-    int cpt, ppr, G, S, ldk, max_slice;
+    int cpt, ppr, G, S, ldk, max_slice, groups;
     size_t dyn;
 };
 
@@ -137,11 +137,22 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
     int bps = 0, st = 0;
     e = fit_attrs_any(p->cpt, vec, &bps, &st);
     if (e != cudaSuccess) return e;
-    const size_t stage = (size_t)p->ppr * N * 16;
     const long avail = (long)optin - st - (long)vec - 1024;
+    // Preferred: the two-group loading pass with one panel per ring stage and an
+    // even stage count; otherwise one group with PPR panels per stage.
+    p->groups = 1;
+    size_t stage = (size_t)N * 16;
     int S = avail > 0 ? (int)(avail / (long)stage) : 0;
     if (S > kMaxStages) S = kMaxStages;
-    if (S < 2) S = 0;
+    S &= ~1;
+    if (p->cpt >= 2 && p->cpt <= 4 && S >= 4) {
+        p->groups = 2;
+    } else {
+        stage = (size_t)p->ppr * N * 16;
+        S = avail > 0 ? (int)(avail / (long)stage) : 0;
+        if (S > kMaxStages) S = kMaxStages;
+        if (S < 2) S = 0;
+    }
     p->S = S;
     p->dyn = vec + (size_t)S * stage;
     e = fit_attrs_any(p->cpt, p->dyn, &bps, &st);
@@ -206,6 +217,7 @@ inline FitArgs make_args(const Workspace& w, const Plan& p, int M, int N, int K,
     a.timeout_ns = (unsigned long long)(timeout_s * 1e9);
     a.timing = nullptr;
     a.tma_stages = p.S;
+    a.dot_groups = p.groups;
     a.ldk = p.ldk;
     a.max_slice = p.max_slice;
     a.redundant_max = kRedundantMax;
