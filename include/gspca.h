@@ -79,6 +79,16 @@ typedef struct {
                                iterations for component k and ignore the test */
     int grid_ctas;          /* CTAs of the persistent kernel; 0 = automatic */
     double timeout_s;       /* limit of every device-side wait; 0 = 2 seconds */
+    int cluster_ctas;       /* batched form: CTAs per problem team (1, 2, 4, 8 or 16);
+                               0 = chosen by the library's autotuner */
+    int batch_pass;         /* batched form: loading pass of the iterations; 1 = independent
+                               warp groups (no CTA-wide barrier per round), 2 = CTA-wide
+                               rounds through the shared-memory TMA ring; 0 = autotuned */
+    int test_stall;         /* testing only, default 0: when 1, the first wait on the shared-
+                               memory ring in every pass first waits for a device word that
+                               nothing sets, so the wait limit (timeout_s) runs out and the
+                               call reports GSPCA_ERR_TIMEOUT; exercises the timeout path
+                               without a fault */
 } gspca_opts;
 
 /* Per-call record of the last fit on a handle (host memory). */
@@ -92,6 +102,8 @@ typedef struct {
                                pass, deflation write, Gram-Schmidt factor reads) */
     double kernel_ms;       /* device time of the persistent kernel, from CUDA events recorded
                                around its launch on the caller's stream */
+    int team_ctas;          /* batched form: CTAs per problem team; single fit: grid_ctas */
+    int batch_pass;         /* batched form: loading pass used (1 or 2, see gspca_opts); else 0 */
 } gspca_info;
 
 /* Create a handle on `device` with workspace for problems up to
@@ -139,11 +151,44 @@ typedef struct {
 } gspca_problem;
 
 /* Fit `count` independent problems (problems[] is a HOST array of
- * descriptors) with one algorithm, tolerance and iteration cap.  The batch
- * runs as one persistent launch that takes problems from a device work
- * queue, largest first.  Returns the worst per-problem status. */
+ * descriptors; every pointer inside is a device pointer) with one algorithm,
+ * tolerance and iteration cap.  Not in the paper: the same per-component loop
+ * (Sec. 2.2 / 2.3) run for many small problems at once.
+ *
+ * Execution: one persistent launch per 256 problems.  The grid is made of
+ * thread-block clusters; each cluster is a team of cluster_ctas CTAs that
+ * takes the next problem from a device work queue (largest M*N first), packs
+ * its X, fits it and writes its T, P, lambda, iters and status, then takes the
+ * next.  opts->center must be GSPCA_CENTER_NONE and opts->iters_lock NULL.
+ * Requirements per problem: 1 <= K <= min(M, N), N <= 1024, ldx >= M,
+ * M <= max_M, N <= max_N and K <= max_K of the handle; X, T, P, lambda
+ * non-NULL.  count >= 1.
+ *
+ * Team size: opts->cluster_ctas, or (0) the autotuner's choice for this list
+ * of shapes: on the first call with a new shape list that is not being
+ * captured, every feasible team size is timed on the real batch and the
+ * fastest is kept in the handle (the outputs are those of a final run with
+ * it).  The batch workspace (one private panel copy of the largest problem per
+ * cluster) is allocated, or grown, by calls that are not being captured and
+ * owned by the handle.
+ *
+ * gspca_fit_batched synchronises `stream` and returns the worst
+ * per-problem status (GSPCA_OK < GSPCA_WARN_NOT_CONVERGED <
+ * GSPCA_ERR_DEGENERATE < GSPCA_ERR_TIMEOUT). */
 gspca_status gspca_fit_batched(gspca_t h, void *stream, const gspca_problem *problems, int count,
                                double tol, int max_iter, gspca_algo algo, const gspca_opts *opts);
+
+/* Asynchronous form of gspca_fit_batched, usable inside CUDA stream capture:
+ * enqueues the batch on `stream` and returns GSPCA_OK without waiting; the
+ * per-problem status words and *worst_status (a device int, nullable) are
+ * written by the GPU.  Under capture the call launches with the team size and
+ * workspace of an earlier uncaptured call on the same shape list (without one
+ * it returns GSPCA_ERR_NOT_SUPPORTED and enqueues nothing); the descriptors are
+ * copied into the launch parameters, so the captured graph does not depend on
+ * problems[] afterwards. */
+gspca_status gspca_fit_batched_async(gspca_t h, void *stream, const gspca_problem *problems,
+                                     int count, double tol, int max_iter, gspca_algo algo,
+                                     const gspca_opts *opts, int *worst_status);
 
 /* Fit without allocating.  The paper has no counterpart to this entry point;
  * it exists for callers that must not allocate device memory themselves or

@@ -30,8 +30,9 @@ GSPCA_ERR_DEGENERATE = 5
 GSPCA_ERR_TIMEOUT = 6
 GSPCA_ERR_NOT_SUPPORTED = 7
 
-EXPORTS = ["gspca_create", "gspca_fit", "gspca_fit_host", "gspca_fit_batched", "gspca_get_info",
-           "gspca_destroy", "gspca_status_string", "gspca_last_cuda_error", "gspca_fit_noalloc"]
+EXPORTS = ["gspca_create", "gspca_fit", "gspca_fit_host", "gspca_fit_batched", "gspca_fit_batched_async",
+           "gspca_get_info", "gspca_destroy", "gspca_status_string", "gspca_last_cuda_error",
+           "gspca_fit_noalloc"]
 
 _ALGOS = {"nipals": GSPCA_NIPALS, "gs": GSPCA_GS, GSPCA_NIPALS: GSPCA_NIPALS, GSPCA_GS: GSPCA_GS}
 _DTYPES = {"f32": GSPCA_F32, "bf16": GSPCA_BF16, GSPCA_F32: GSPCA_F32, GSPCA_BF16: GSPCA_BF16}
@@ -48,14 +49,15 @@ class GspcaError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("center", ctypes.c_int), ("iters_lock", ctypes.POINTER(ctypes.c_int)),
-                ("grid_ctas", ctypes.c_int), ("timeout_s", ctypes.c_double)]
+                ("grid_ctas", ctypes.c_int), ("timeout_s", ctypes.c_double),
+                ("cluster_ctas", ctypes.c_int), ("batch_pass", ctypes.c_int), ("test_stall", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("found", ctypes.c_int), ("total_iters", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_int), ("grid_ctas", ctypes.c_int),
                 ("block_threads", ctypes.c_int), ("alg_bytes", ctypes.c_double),
-                ("kernel_ms", ctypes.c_double)]
+                ("kernel_ms", ctypes.c_double), ("team_ctas", ctypes.c_int), ("batch_pass", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):
@@ -84,6 +86,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.gspca_fit.argtypes = fit_args
     lib.gspca_fit_host.argtypes = fit_args
     lib.gspca_fit_batched.argtypes = [vp, vp, ctypes.POINTER(Problem), i, d, i, i, ctypes.POINTER(Opts)]
+    lib.gspca_fit_batched_async.argtypes = [vp, vp, ctypes.POINTER(Problem), i, d, i, i, ctypes.POINTER(Opts), vp]
     lib.gspca_fit_noalloc.argtypes = fit_args[1:]
     lib.gspca_fit_noalloc.restype = i
     lib.gspca_get_info.argtypes = [vp, ctypes.POINTER(Info)]
@@ -93,7 +96,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.gspca_last_cuda_error.argtypes = []
     lib.gspca_last_cuda_error.restype = ctypes.c_char_p
     for name in ("gspca_create", "gspca_fit", "gspca_fit_host", "gspca_fit_batched",
-                 "gspca_get_info", "gspca_destroy"):
+                 "gspca_fit_batched_async", "gspca_get_info", "gspca_destroy"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -113,11 +116,14 @@ def last_cuda_error() -> str:
 gspca_last_cuda_error = last_cuda_error
 
 
-def _opts(center=0, iters_lock=None, grid_ctas=0, timeout_s=0.0):
+def _opts(center=0, iters_lock=None, grid_ctas=0, timeout_s=0.0, cluster_ctas=0, test_stall=0, batch_pass=0):
     o = Opts()
+    o.batch_pass = int(batch_pass)
+    o.test_stall = int(test_stall)
     o.center = int(center)
     o.grid_ctas = int(grid_ctas)
     o.timeout_s = float(timeout_s)
+    o.cluster_ctas = int(cluster_ctas)
     keep = None
     if iters_lock is not None:
         keep = (ctypes.c_int * len(iters_lock))(*[int(v) for v in iters_lock])
@@ -171,7 +177,7 @@ class FitResult:
 
 def gspca_fit(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="gs",
               center: int = 0, iters_lock=None, want_R: bool = False, grid_ctas: int = 0,
-              timeout_s: float = 0.0, stream=None, check: bool = True) -> FitResult:
+              timeout_s: float = 0.0, stream=None, check: bool = True, test_stall: int = 0) -> FitResult:
     """Fit K components of X (a float32 CUDA tensor, any 2-D strided layout)."""
     import torch
 
@@ -190,7 +196,7 @@ def gspca_fit(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="
     R = torch.empty((N, M), device=dev, dtype=torch.float32).t() if want_R else None
     if stream is None:
         stream = torch.cuda.current_stream(dev).cuda_stream
-    o, keep = _opts(center, iters_lock, grid_ctas, timeout_s)
+    o, keep = _opts(center, iters_lock, grid_ctas, timeout_s, 0, test_stall)
     st = load().gspca_fit(ctypes.c_void_p(h), ctypes.c_void_p(stream), ctypes.c_void_p(X.data_ptr()),
                           layout, int(ldx), M, N, int(K), float(tol), int(max_iter), _ALGOS[algo],
                           ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(P.data_ptr()),
@@ -281,48 +287,86 @@ class Handle:
             pass
 
 
+class Batch:
+    """Descriptors and output tensors of a batch of independent problems.
+
+    `problems` is a list of dicts with a float32 CUDA tensor "X" (a row-major X is copied
+    to column-major here) and "K".  `results` holds, per problem, a FitResult whose T, P,
+    lam, iters and status (a 1-element int32 tensor) the library writes."""
+
+    def __init__(self, problems):
+        import torch
+
+        self.descs = (Problem * len(problems))()
+        self.keep = []
+        self.outs = []
+        for i, pr in enumerate(problems):
+            X = pr["X"]
+            if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32
+                    and X.dim() == 2):
+                raise TypeError("each X must be a 2-D float32 CUDA tensor")
+            layout, ldx = _layout_of(X)
+            if layout != GSPCA_COL_MAJOR:
+                X = X.t().contiguous().t()
+                ldx = X.shape[0]
+            self.keep.append(X)
+            M, N = X.shape
+            K = int(pr["K"])
+            dev = X.device
+            T = torch.zeros((K, M), device=dev, dtype=torch.float32).t()
+            P = torch.zeros((K, N), device=dev, dtype=torch.float32).t()
+            lam = torch.zeros(K, device=dev, dtype=torch.float64)
+            iters = torch.zeros(K, device=dev, dtype=torch.int32)
+            st = torch.full((1,), -1, device=dev, dtype=torch.int32)
+            d = self.descs[i]
+            d.X, d.ldx, d.M, d.N, d.K = X.data_ptr(), int(ldx), M, N, K
+            d.T, d.P, d.lambda_, d.iters, d.status = (T.data_ptr(), P.data_ptr(), lam.data_ptr(),
+                                                      iters.data_ptr(), st.data_ptr())
+            self.outs.append(FitResult(T, P, lam, iters, None, st, {}))
+
+    def __len__(self):
+        return len(self.outs)
+
+    @property
+    def results(self):
+        return self.outs
+
+
 def gspca_fit_batched(h: int, problems, tol: float = 1e-6, max_iter: int = 1000, algo="gs",
-                      grid_ctas: int = 0, timeout_s: float = 0.0, stream=None, check: bool = True):
-    """Fit independent problems in one launch.  `problems` is a list of dicts with a float32
-    CUDA tensor "X" (any column- or row-major layout is packed column-major here) and "K";
-    returns a list of FitResult (T, P, lam, iters, status per problem) and the batch status."""
+                      cluster_ctas: int = 0, timeout_s: float = 0.0, stream=None, check: bool = True,
+                      test_stall: int = 0, batch_pass: int = 0):
+    """Fit independent problems in one persistent launch (per 256 problems) and wait.
+    `problems` is a Batch or a list accepted by Batch; returns (Batch, worst status)."""
     import torch
 
-    descs = (Problem * len(problems))()
-    outs = []
-    keep = []
-    for i, pr in enumerate(problems):
-        X = pr["X"]
-        if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
-            raise TypeError("each X must be a 2-D float32 CUDA tensor")
-        layout, ldx = _layout_of(X)
-        if layout != GSPCA_COL_MAJOR:
-            X = X.t().contiguous().t()
-            ldx = X.shape[0]
-        keep.append(X)
-        M, N = X.shape
-        K = int(pr["K"])
-        dev = X.device
-        T = torch.zeros((K, M), device=dev, dtype=torch.float32).t()
-        P = torch.zeros((K, N), device=dev, dtype=torch.float32).t()
-        lam = torch.zeros(K, device=dev, dtype=torch.float64)
-        iters = torch.zeros(K, device=dev, dtype=torch.int32)
-        st = torch.zeros(1, device=dev, dtype=torch.int32)
-        d = descs[i]
-        d.X, d.ldx, d.M, d.N, d.K = X.data_ptr(), int(ldx), M, N, K
-        d.T, d.P, d.lambda_, d.iters, d.status = (T.data_ptr(), P.data_ptr(), lam.data_ptr(),
-                                                  iters.data_ptr(), st.data_ptr())
-        outs.append((T, P, lam, iters, st))
+    b = problems if isinstance(problems, Batch) else Batch(problems)
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
-    o, _ = _opts(0, None, grid_ctas, timeout_s)
-    st = load().gspca_fit_batched(ctypes.c_void_p(h), ctypes.c_void_p(stream), descs, len(problems),
+    o, _ = _opts(0, None, 0, timeout_s, cluster_ctas, test_stall, batch_pass)
+    st = load().gspca_fit_batched(ctypes.c_void_p(h), ctypes.c_void_p(stream), b.descs, len(b),
                                   float(tol), int(max_iter), _ALGOS[algo], ctypes.byref(o))
     if check and st not in (GSPCA_OK, GSPCA_WARN_NOT_CONVERGED, GSPCA_ERR_DEGENERATE):
         raise GspcaError(st, "gspca_fit_batched")
     info = gspca_get_info(h)
-    res = [FitResult(T, P, lam, iters, None, s, info) for (T, P, lam, iters, s) in outs]
-    return res, st
+    for r in b.outs:
+        r.info = info
+    return b, st
+
+
+def gspca_fit_batched_async(h: int, batch: Batch, tol: float = 1e-6, max_iter: int = 1000, algo="gs",
+                            cluster_ctas: int = 0, timeout_s: float = 0.0, worst=None, stream=None,
+                            batch_pass: int = 0) -> int:
+    """Enqueue a batch without waiting (usable inside CUDA stream capture after one uncaptured
+    call on the same shapes).  `worst` is an optional 1-element int32 CUDA tensor that receives
+    the worst per-problem status.  Returns the enqueue status."""
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    o, _ = _opts(0, None, 0, timeout_s, cluster_ctas, 0, batch_pass)
+    return load().gspca_fit_batched_async(ctypes.c_void_p(h), ctypes.c_void_p(stream), batch.descs, len(batch),
+                                          float(tol), int(max_iter), _ALGOS[algo], ctypes.byref(o),
+                                          ctypes.c_void_p(worst.data_ptr()) if worst is not None else None)
 
 
 NOALLOC_SCRATCH_BYTES = 64 << 20

@@ -78,10 +78,14 @@ struct FitArgs {
     unsigned long long timeout_ns;
     unsigned long long* timing;  // phase-time accumulators (instrumented builds only), nullable
     int tma_stages;           // TMA ring stages (0 = panels loaded straight into registers)
+    int ring_bytes;           // shared-memory bytes reserved for the ring (vectors follow)
     int dot_groups;           // 2: the loading pass runs as two independent 256-thread groups
     int ldk;                  // shared-memory length of the k-vectors (>= K)
     int max_slice;            // shared-memory length of the N slice (>= n1 - n0)
     int redundant_max;        // reduce k-vectors in every CTA when k <= this
+    int narrow;               // 1: the loading pass is pass_lds (N <= 1024, no CTA ring)
+    const int* stall_word;    // testing, nullable: a word nothing sets; the first ring wait of
+                              // every pass first waits for it (bounded) and so runs out
 };
 
 struct __align__(16) SmemFit {
@@ -99,10 +103,12 @@ struct __align__(16) SmemFit {
     int flag;
     int sel;
     int stop;
+    int mbar_live;
 #ifdef GSPCA_PHASE_TIMING
     unsigned long long tacc[16];
     unsigned long long tlast;
     int tcur;
+    int tmark;  // this CTA records phase times
 #endif
 };
 
@@ -112,7 +118,7 @@ struct __align__(16) SmemFit {
 #ifdef GSPCA_PHASE_TIMING
 #define PHASE_MARK(id)                                      \
     do {                                                    \
-        if (blockIdx.x == 0 && threadIdx.x == 0) {          \
+        if (threadIdx.x == 0 && sm.tmark) {                 \
             const unsigned long long t_ = globaltimer_ns(); \
             sm.tacc[sm.tcur] += t_ - sm.tlast;              \
             sm.tlast = t_;                                  \
@@ -166,11 +172,29 @@ __device__ __forceinline__ void ring_prefetch(const FitArgs& f, Ring& rg, int p0
     for (int i = (int)(rg.issued - rg.used); i < rg.S && i < nrounds; ++i) ring_issue(f, rg, p0, p1, ppr, i);
 }
 
-// Before leaving the kernel early: wait (bounded) for the copies still in flight.
+// A ring wait that gave up after the caller's limit is reported as a timeout,
+// but the copy it waited for was issued and normally lands a little later: the
+// stage is awaited again, for at most this long, before it is read, refilled
+// or abandoned, so that no copy is still in flight when its stage (or the
+// CTA's shared memory) is reused.
+constexpr unsigned long long kSettleNs = 1000000000ull;
+
+// Testing hook: wait, bounded by the caller's limit, for a word that nothing
+// sets; returns false when the limit runs out.
+__device__ __forceinline__ bool stall_wait(const FitArgs& f) {
+    const uint64_t t0 = globaltimer_ns();
+    while (ld_relaxed_s32(f.stall_word) == 0)
+        if (globaltimer_ns() - t0 > f.timeout_ns) return false;
+    return true;
+}
+
+// Wait (bounded) for the copies still in flight (before leaving, or before the
+// ring is set up again).
 __device__ __forceinline__ void ring_drain(const FitArgs& f, const Ring& rg) {
+    const unsigned long long bound = f.timeout_ns > kSettleNs ? f.timeout_ns : kSettleNs;
     if (threadIdx.x == 0)
         for (unsigned q = rg.used; q < rg.issued; ++q)
-            if (!mbar_wait(rg.bar(q), (q / rg.S) & 1u, f.timeout_ns)) break;
+            if (!mbar_wait(rg.bar(q), (q / rg.S) & 1u, bound)) break;
     __syncthreads();
 }
 
@@ -210,7 +234,11 @@ __device__ __forceinline__ bool row_pass(const FitArgs& f, SmemFit& sm, Ring& rg
         float4 d[PPR][CPT];
         if (tma) {
             const unsigned q = base + (unsigned)round;
-            if (!mbar_wait(rg.bar(q), (q / rg.S) & 1u, f.timeout_ns)) ok = 0;
+            if (f.stall_word && round == 0 && !stall_wait(f)) ok = 0;
+            if (!mbar_wait(rg.bar(q), (q / rg.S) & 1u, f.timeout_ns)) {
+                ok = 0;  // reported; the stage is still awaited before it is read or refilled
+                mbar_wait(rg.bar(q), (q / rg.S) & 1u, kSettleNs);
+            }
             const float* st = rg.stage(q);
 #pragma unroll
             for (int pp = 0; pp < PPR; ++pp) {
@@ -383,7 +411,11 @@ __device__ __forceinline__ bool pass_dot2(const FitArgs& f, SmemFit& sm, Ring& r
     for (int round = grp; round < nrounds; round += 2) {
         const int p = p0 + round;
         const unsigned q = base + (unsigned)round;
-        if (!mbar_wait(rg.bar(q), (q / rg.S) & 1u, f.timeout_ns)) ok = 0;
+        if (f.stall_word && round == grp && !stall_wait(f)) ok = 0;
+        if (!mbar_wait(rg.bar(q), (q / rg.S) & 1u, f.timeout_ns)) {
+            ok = 0;  // reported; the stage is still awaited before it is read or refilled
+            mbar_wait(rg.bar(q), (q / rg.S) & 1u, kSettleNs);
+        }
         const float* st = rg.stage(q);
         float4 d[C2];
 #pragma unroll
@@ -455,7 +487,302 @@ __device__ __forceinline__ bool pass_dot2(const FitArgs& f, SmemFit& sm, Ring& r
     return all_ok != 0;
 }
 
+// Loading pass (kPassDot) for narrow problems, N <= 256 * TW, with no
+// CTA-wide barrier inside the pass.  The 16 warps form 16 / TW groups of TW
+// warps; group g takes rounds g, g + 16/TW, ... of PP consecutive panels.
+// Warp wi of a group owns the column chunk [256 wi, 256 wi + cw) (TW > 1) or
+// all N columns (TW == 1); lane l holds columns chunk + l + 32 j (j < NJW) of
+// u' and of the group's s' partials.
+//
+// Every lane streams its own 16-byte pieces of R (4 rows x 1 column) through
+// a private ring of kLdsStages shared-memory stages with asynchronous copies
+// (cp.async, one commit group per round), issued kLdsStages rounds ahead, so
+// no register holds data in flight and no lane waits for another lane's copy.
+// Per round: v' for the 4 PP rows (one multi-value butterfly per warp, then,
+// for TW > 1, the TW warp partials summed through shared memory behind a named
+// barrier of the group), then s' += R_round^T v' from the same stage.
+//
+// Shared memory (dyn): 16 warps x kLdsStages stages of 4 KB; at the end of the
+// pass the same bytes hold the groups' s' partials (16 / TW x N floats), summed
+// in a fixed order into pA[0..N).  sc = sum v'^2 over the CTA's rows.  Returns
+// false (in every thread) if the testing stall hook ran out.
+constexpr int kLdsStages = 3;
+constexpr int kLdsStageBytes = 4096;
+constexpr int kLdsBytes = kMaxWarps * kLdsStages * kLdsStageBytes;
+
+template <int NJW, int TW>
+struct LdsTraits {
+    static constexpr int PP = (NJW == 8) ? 1 : 8 / NJW;  // panels per round (PP * NJW = 8 pieces per lane)
+    static constexpr int CW = 32 * NJW;                  // column chunk of a warp
+    static constexpr int NG = kMaxWarps / TW;            // groups
+    static constexpr int GT = 32 * TW;                   // threads per group
+    static constexpr int V = 4 * PP;                     // row values per round
+    static_assert(PP * CW * 16 == kLdsStageBytes, "one stage holds a round");
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int NJW, int TW>
+__device__ __forceinline__ bool pass_lds(const FitArgs& f, SmemFit& sm, int p0, int p1, const float* __restrict__ u_in,
+                                         float* pA, ff& sc, unsigned char* dyn) {
+    using B = LdsTraits<NJW, TW>;
+    constexpr int PP = B::PP, CW = B::CW, NG = B::NG, GT = B::GT, V = B::V, SW = kLdsStages;
+    constexpr int SHIFT = 5 - Log2<V>::value;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int grp = warp / TW, wi = warp % TW;
+    const int N = f.N;
+    const int c0 = (TW == 1) ? 0 : wi * CW;  // first column of the warp's chunk
+    // its width; 0 for the last warps of a group when N <= 256 (TW - 1): those
+    // warps copy and read nothing but still take part in the group's barriers
+    const int cw = (TW == 1) ? N : max(0, min(CW, N - c0));
+    unsigned char* stages = dyn + (size_t)warp * SW * kLdsStageBytes;
+    int ok = 1;
+    if (f.stall_word && !stall_wait(f)) ok = 0;
+    float u[NJW], s[NJW];
+#pragma unroll
+    for (int j = 0; j < NJW; ++j) {
+        const int c = lane + 32 * j;
+        u[j] = c < cw ? ldcg(u_in + c0 + c) : 0.f;
+        s[j] = 0.f;
+    }
+    ff my = ff_zero();
+    const int npan = p1 - p0;
+    const int nrounds = (npan + PP - 1) / PP;
+    const int nr = nrounds > grp ? (nrounds - grp + NG - 1) / NG : 0;  // this group's rounds
+    // piece (pp, j) of a round: panel pb + pp, column c0 + lane + 32 j, at
+    // stage offset (pp * NJW + j) * 512 + lane * 16 (a warp's copies of one
+    // piece index are 512 contiguous bytes on both sides)
+    auto issue = [&](int i) {
+        if (i < nr) {
+            unsigned char* st = stages + (size_t)(i % SW) * kLdsStageBytes;
+            const int pb = p0 + (grp + NG * i) * PP;
+#pragma unroll
+            for (int pp = 0; pp < PP; ++pp)
+#pragma unroll
+                for (int j = 0; j < NJW; ++j) {
+                    const int c = lane + 32 * j;
+                    if (pb + pp < p1 && c < cw)
+                        cp_async16(st + (pp * NJW + j) * 512 + lane * 16, f.R + ((size_t)(pb + pp) * N + c0 + c) * 4);
+                }
+        }
+        cp_async_commit();  // one group per round (possibly empty) keeps the counts uniform
+    };
+#pragma unroll
+    for (int i = 0; i < SW; ++i) issue(i);
+    for (int i = 0; i < nr; ++i) {
+        const int pb = p0 + (grp + NG * i) * PP;
+        cp_async_wait<SW - 1>();  // this lane's pieces of round i have landed
+        const unsigned char* sb = stages + (size_t)(i % SW) * kLdsStageBytes + lane * 16;
+        float4 d[PP][NJW];
+#pragma unroll
+        for (int pp = 0; pp < PP; ++pp)
+#pragma unroll
+            for (int j = 0; j < NJW; ++j) {
+                const int c = lane + 32 * j;
+                d[pp][j] = (pb + pp < p1 && c < cw) ? *reinterpret_cast<const float4*>(sb + (pp * NJW + j) * 512)
+                                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        float acc[V];
+#pragma unroll
+        for (int pp = 0; pp < PP; ++pp) {
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+            for (int j = 0; j < NJW; ++j) {
+                a0 = fmaf(d[pp][j].x, u[j], a0);
+                a1 = fmaf(d[pp][j].y, u[j], a1);
+                a2 = fmaf(d[pp][j].z, u[j], a2);
+                a3 = fmaf(d[pp][j].w, u[j], a3);
+            }
+            acc[pp * 4 + 0] = a0;
+            acc[pp * 4 + 1] = a1;
+            acc[pp * 4 + 2] = a2;
+            acc[pp * 4 + 3] = a3;
+        }
+        // every piece of the stage has been used (so read): refill it with round i + SW
+        issue(i + SW);
+        const float wsum = warp_multi_reduce<V>(acc, lane);  // value lane >> SHIFT
+        const int par = i & 1;
+        if ((lane & ((1 << SHIFT) - 1)) == 0) sm.tmpf[warp][par * 32 + (lane >> SHIFT)] = wsum;
+        if (TW == 1)
+            __syncwarp();
+        else
+            named_barrier(1 + grp, GT);
+        float v[V];
+#pragma unroll
+        for (int k4 = 0; k4 < V; k4 += 4) {
+            float4 t = *reinterpret_cast<const float4*>(&sm.tmpf[grp * TW][par * 32 + k4]);
+#pragma unroll
+            for (int w = 1; w < TW; ++w) {
+                const float4 o = *reinterpret_cast<const float4*>(&sm.tmpf[grp * TW + w][par * 32 + k4]);
+                t.x += o.x;
+                t.y += o.y;
+                t.z += o.z;
+                t.w += o.w;
+            }
+            v[k4] = t.x;
+            v[k4 + 1] = t.y;
+            v[k4 + 2] = t.z;
+            v[k4 + 3] = t.w;
+        }
+        if (wi == 0 && lane < V) {
+            float mine = v[0];
+#pragma unroll
+            for (int k2 = 1; k2 < V; ++k2)
+                if (k2 == lane) mine = v[k2];
+            const int p = pb + lane / 4;
+            if (p < p1) {
+                f.vraw[(size_t)p * 4 + (lane & 3)] = mine;
+                my = ff_add(my, ff_sqr(mine));
+            }
+        }
+#pragma unroll
+        for (int pp = 0; pp < PP; ++pp)
+#pragma unroll
+            for (int j = 0; j < NJW; ++j) {
+                s[j] = fmaf(d[pp][j].x, v[pp * 4 + 0], s[j]);
+                s[j] = fmaf(d[pp][j].y, v[pp * 4 + 1], s[j]);
+                s[j] = fmaf(d[pp][j].z, v[pp * 4 + 2], s[j]);
+                s[j] = fmaf(d[pp][j].w, v[pp * 4 + 3], s[j]);
+            }
+    }
+    cp_async_wait<0>();  // only empty groups remain; nothing may land after this
+    // groups' s' partials -> pA (fixed order); sum v'^2 over the CTA
+    __syncthreads();  // every stage consumed: the stage memory becomes the exchange area
+    float* xch = reinterpret_cast<float*>(dyn);
+#pragma unroll
+    for (int j = 0; j < NJW; ++j) {
+        const int c = lane + 32 * j;
+        if (c < cw) xch[(size_t)grp * N + c0 + c] = s[j];
+    }
+    my = warp_sum_ff(my);
+    if (lane == 0) sm.ffw[warp] = my;
+    const int all_ok = __syncthreads_and(ok);
+    for (int c = tid; c < N; c += blockDim.x) {
+        float t = xch[c];
+        for (int g2 = 1; g2 < NG; ++g2) t += xch[(size_t)g2 * N + c];
+        pA[c] = t;
+    }
+    if (warp == 0) {
+        ff t = lane < kMaxWarps ? sm.ffw[lane] : ff_zero();
+#pragma unroll
+        for (int o = 8; o >= 1; o >>= 1) t = ff_add(t, ff_shfl_xor(t, o));
+        if (lane == 0) sm.sff[3] = t;
+    }
+    __syncthreads();
+    sc = sm.sff[3];
+    __syncthreads();
+    return all_ok != 0;
+}
+
+// pass_lds for the column count of f (N <= 512 when CPT == 1, N <= 1024 when
+// CPT == 2).
+template <int CPT>
+__device__ __forceinline__ bool pass_narrow(const FitArgs& f, SmemFit& sm, int p0, int p1, const float* u_in,
+                                            float* pA, ff& sc, unsigned char* dyn) {
+    const int nj = (f.N + 31) / 32;
+    if constexpr (CPT == 1) {
+        if (nj <= 1) return pass_lds<1, 1>(f, sm, p0, p1, u_in, pA, sc, dyn);
+        if (nj <= 2) return pass_lds<2, 1>(f, sm, p0, p1, u_in, pA, sc, dyn);
+        if (nj <= 4) return pass_lds<4, 1>(f, sm, p0, p1, u_in, pA, sc, dyn);
+        if (nj <= 8) return pass_lds<8, 1>(f, sm, p0, p1, u_in, pA, sc, dyn);
+        return pass_lds<8, 2>(f, sm, p0, p1, u_in, pA, sc, dyn);
+    } else {
+        return pass_lds<8, 4>(f, sm, p0, p1, u_in, pA, sc, dyn);
+    }
+}
+
 // ------------------------------------------------------------------ small products
+
+// Row-major k-column factors (V, U, W) with a power-of-two leading dimension
+// lda in [4, 128] are read as float4 chunks: lda / 4 lanes cover one row, a
+// warp load covers 32 / (lda / 4) consecutive rows (512 contiguous bytes), and
+// a lane issues kVecRows such loads before using any of them.
+constexpr int kVecRows = 8;
+
+__device__ __forceinline__ bool vec_lda(int lda) { return lda >= 4 && lda <= 128 && (lda & (lda - 1)) == 0; }
+
+template <class Y>
+__device__ __forceinline__ void rows_times_matrix_vec(const float* A, int lda, int r0, int r1, int kk, Y y,
+                                                      float* dst, SmemFit& sm) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int L4 = lda >> 2, rpw = 32 / L4, sub = lane / L4, cq = lane % L4;
+    const bool live = 4 * cq < kk;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int rb = r0 + warp * rpw * kVecRows; rb < r1; rb += nw * rpw * kVecRows) {
+        float4 a[kVecRows];
+        float yr[kVecRows];
+#pragma unroll
+        for (int u = 0; u < kVecRows; ++u) {
+            const int r = rb + u * rpw + sub;
+            const bool ok = r < r1;
+            yr[u] = ok ? y(r) : 0.f;
+            a[u] = (ok && live) ? __ldcg(reinterpret_cast<const float4*>(A + (size_t)r * lda) + cq)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kVecRows; ++u) {
+            acc.x = fmaf(a[u].x, yr[u], acc.x);
+            acc.y = fmaf(a[u].y, yr[u], acc.y);
+            acc.z = fmaf(a[u].z, yr[u], acc.z);
+            acc.w = fmaf(a[u].w, yr[u], acc.w);
+        }
+    }
+    for (int o = 16; o >= L4; o >>= 1) {
+        acc.x += __shfl_xor_sync(kFull, acc.x, o);
+        acc.y += __shfl_xor_sync(kFull, acc.y, o);
+        acc.z += __shfl_xor_sync(kFull, acc.z, o);
+        acc.w += __shfl_xor_sync(kFull, acc.w, o);
+    }
+    if (lane < L4) *reinterpret_cast<float4*>(&sm.tmpf[warp][4 * lane]) = acc;
+    __syncthreads();
+    for (int t = tid; t < kk; t += blockDim.x) {
+        float s = 0.f;
+        for (int w = 0; w < nw; ++w) s += sm.tmpf[w][t];
+        dst[t] = s;
+    }
+    __syncthreads();
+}
+
+template <class Pre, class Fn>
+__device__ __forceinline__ void matrix_times_vector_vec(const float* A, int lda, int r0, int r1, int kk,
+                                                        const float* x, Pre pre, Fn fn) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int L4 = lda >> 2, rpw = 32 / L4, sub = lane / L4, cq = lane % L4;
+    const int j = 4 * cq;
+    const float4 xv = make_float4(j < kk ? x[j] : 0.f, j + 1 < kk ? x[j + 1] : 0.f, j + 2 < kk ? x[j + 2] : 0.f,
+                                  j + 3 < kk ? x[j + 3] : 0.f);
+    const bool live = j < kk;
+    for (int rb = r0 + warp * rpw * kVecRows; rb < r1; rb += nw * rpw * kVecRows) {
+        float4 a[kVecRows];
+        float pv[kVecRows];
+#pragma unroll
+        for (int u = 0; u < kVecRows; ++u) {
+            const int r = rb + u * rpw + sub;
+            const bool ok = r < r1;
+            pv[u] = (ok && cq == 0) ? pre(r) : 0.f;
+            a[u] = (ok && live) ? __ldcg(reinterpret_cast<const float4*>(A + (size_t)r * lda) + cq)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kVecRows; ++u) {
+            // columns at or past kk hold data of other components: weight 0 and masked value
+            float d = (j < kk ? a[u].x * xv.x : 0.f);
+            d = (j + 1 < kk) ? fmaf(a[u].y, xv.y, d) : d;
+            d = (j + 2 < kk) ? fmaf(a[u].z, xv.z, d) : d;
+            d = (j + 3 < kk) ? fmaf(a[u].w, xv.w, d) : d;
+            for (int o = 1; o < L4; o <<= 1) d += __shfl_xor_sync(kFull, d, o);
+            const int r = rb + u * rpw + sub;
+            if (cq == 0 && r < r1) fn(r, d, pv[u]);
+        }
+    }
+}
 
 // dst[j] = sum_{r in [r0, r1)} A[r*lda + j] * y(r) for j < kk, FP32 within the CTA.
 // A warp takes rows r0 + warp + 16 i (i < 8 per block) and issues every load
@@ -463,6 +790,10 @@ __device__ __forceinline__ bool pass_dot2(const FitArgs& f, SmemFit& sm, Ring& r
 template <class Y>
 __device__ __forceinline__ void rows_times_matrix(const float* A, int lda, int r0, int r1, int kk, Y y, float* dst,
                                                   SmemFit& sm) {
+    if (vec_lda(lda)) {
+        rows_times_matrix_vec(A, lda, r0, r1, kk, y, dst, sm);
+        return;
+    }
     constexpr int MAXR = 8;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     for (int j0 = 0; j0 < kk; j0 += 128) {
@@ -505,6 +836,10 @@ __device__ __forceinline__ void rows_times_matrix(const float* A, int lda, int r
 template <class Pre, class Fn>
 __device__ __forceinline__ void matrix_times_vector(const float* A, int lda, int r0, int r1, int kk, const float* x,
                                                     Pre pre, Fn fn) {
+    if (vec_lda(lda)) {
+        matrix_times_vector_vec(A, lda, r0, r1, kk, x, pre, fn);
+        return;
+    }
     constexpr int MAXR = 8, MAXJ = 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int rb = r0 + warp; rb < r1; rb += nw * MAXR) {
@@ -573,10 +908,10 @@ __device__ __forceinline__ ff block_sum_ff(ff v, SmemFit& sm) {
 // ...; lane l loads columns l and l+32 of a block; a thread sums its rows in
 // FP32, the 16 warp sums of a column combine in a fixed float-float butterfly.
 template <class Col>
-__device__ __forceinline__ void gather_reduce(const FitArgs& f, SmemFit& sm, int nq, int s0, int s1,
+__device__ __forceinline__ void gather_reduce(const FitArgs& f, SmemFit& sm, int G, int nq, int s0, int s1,
                                               const float* part, int L, int nv, Col col, float* out) {
     constexpr int MAXI = 10, MAXJ = 2, NW = kMaxWarps;
-    const int G = gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     float2 q0 = make_float2(0.f, 0.f), q1 = make_float2(0.f, 0.f);
     if (t < G) {
         if (nq > 0) q0 = ldcg(f.spart + (size_t)t * 4 + s0);
@@ -633,8 +968,8 @@ __device__ __forceinline__ void gather_reduce(const FitArgs& f, SmemFit& sm, int
 // Sum of column c of a G x L FP32 partial buffer: lane l adds CTA rows
 // l, l+32, ... in FP32 (loads issued together), then a fixed float-float
 // butterfly across the 32 lanes.  Result in every lane.
-__device__ __forceinline__ ff column_sum(const float* part, int L, int c) {
-    const int G = gridDim.x, lane = threadIdx.x & 31;
+__device__ __forceinline__ ff column_sum(const float* part, int G, int L, int c) {
+    const int lane = threadIdx.x & 31;
     float s = 0.f;
 #pragma unroll 8
     for (int r = lane; r < G; r += 32) s += ldcg(part + (size_t)r * L + c);
@@ -643,78 +978,115 @@ __device__ __forceinline__ ff column_sum(const float* part, int L, int c) {
 
 // Columns [c0, c0+nc) reduced once across the whole grid into red[0..nc)
 // (FP64): columns are dealt to the warps of all CTAs in a fixed pattern.
-__device__ __forceinline__ void reduce_cols_distributed(const float* part, int L, int c0, int nc, double* red) {
-    const int G = gridDim.x, g = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ void reduce_cols_distributed(const float* part, int G, int g, int L, int c0, int nc,
+                                                        double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const int gw = g * nw + warp, nwt = G * nw;
     for (int c = gw; c < nc; c += nwt) {
-        const ff t = column_sum(part, L, c0 + c);
+        const ff t = column_sum(part, G, L, c0 + c);
         if (lane == 0) red[c] = ff_to_double(t);
     }
 }
 
-__device__ __forceinline__ void write_scalar(const FitArgs& f, int slot, ff v) {
-    if (threadIdx.x == 0) f.spart[(size_t)blockIdx.x * 4 + slot] = make_float2(v.hi, v.lo);
+__device__ __forceinline__ void write_scalar(const FitArgs& f, int g, int slot, ff v) {
+    if (threadIdx.x == 0) f.spart[(size_t)g * 4 + slot] = make_float2(v.hi, v.lo);
 }
 
-// ------------------------------------------------------------------ kernel
+// ------------------------------------------------------------------ teams
 
-template <int CPT>
-__global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
+// The CTAs that fit one problem together.  TeamGrid: every CTA of a
+// cooperative launch, synchronised by the bounded counter barrier (a failed
+// wait means "leave the kernel").  TeamCluster: the CTAs of one thread-block
+// cluster, synchronised by the hardware cluster barrier (release/acquire at
+// cluster scope orders their global-memory partials).
+//
+// A pass whose bounded ring wait gave up calls fail(): the grid team raises
+// the kernel-wide abort word and leaves at once (the other CTAs see the word
+// inside their barrier waits); the cluster team cannot leave a hardware
+// barrier early, so it records the failure in a per-team word and carries on
+// with a NaN pass scalar, which every CTA of the team reduces to the same
+// "degenerate" exit at the next test.
+struct TeamGrid {
+    int G, g;
+    GridBarrier bar;
+    __device__ __forceinline__ bool sync(unsigned& epoch, int* flag) const { return bar.sync(epoch, flag); }
+    __device__ __forceinline__ bool fail(const FitArgs& f) const {
+        if (threadIdx.x == 0) atomicCAS(f.abort, 0, kStTimeout);
+        return true;
+    }
+};
+
+struct TeamCluster {
+    int G, g;
+    int* failed;  // per-team word, read by the caller after the team's last barrier
+    __device__ __forceinline__ bool sync(unsigned& epoch, int*) const {
+        ++epoch;
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+        return true;
+    }
+    __device__ __forceinline__ bool fail(const FitArgs&) const {
+        if (threadIdx.x == 0) atomicExch(failed, 1);
+        return false;
+    }
+};
+
+struct FitOutcome {
+    int status, found;
+    long long total;
+    bool alive;  // false: a bounded wait gave up, the kernel must leave
+};
+
+// (Re)initialise this CTA's ring for a problem with N columns: S stages of
+// ppr panels each.  Must be called with no copy in flight.
+__device__ __forceinline__ void ring_setup(Ring& rg, SmemFit& sm, unsigned char* dyn_smem, int S, int ppr, int N) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < sm.mbar_live; ++s)
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(&sm.mbar[s])) : "memory");
+        for (int s = 0; s < S; ++s) mbar_init(reinterpret_cast<uint64_t*>(&sm.mbar[s]), 1);
+        sm.mbar_live = S;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    rg.S = S;
+    rg.stage_floats = ppr * N * 4;
+    rg.base = reinterpret_cast<float*>(dyn_smem);
+    rg.mbar = sm.mbar;
+    rg.issued = rg.used = 0;
+}
+
+// Fit one problem (f) with a team of CTAs.  The caller provides the
+// degenerate threshold and this CTA's shared memory; the ring must be set up
+// for f.N.  Writes V, U, W and lambda/iters for k < found; returns the
+// outcome (identical in every CTA of the team).
+template <int CPT, class Team>
+__device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, unsigned char* dyn_smem, Ring& rg,
+                              float threshf, unsigned& epoch) {
     constexpr int PPR = PassShape<CPT>::PPR;
-    __shared__ SmemFit sm;
-    extern __shared__ __align__(128) unsigned char dyn_smem[];
-    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
+    const int G = tm.G, g = tm.g, tid = threadIdx.x, T = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int N = f.N, K = f.K;
     const int p0 = (int)(((long long)g * f.np) / G), p1 = (int)(((long long)(g + 1) * f.np) / G);
     const int r0 = min(p0 * 4, f.M), r1 = min(p1 * 4, f.M);
     const int n0 = (int)(((long long)g * N) / G), n1 = (int)(((long long)(g + 1) * N) / G);
-    const GridBarrier bar{f.flags, f.abort, f.timeout_ns};
     const bool gs = (f.algo == 1);
     float* pA = f.partA + (size_t)g * f.LA;
     float* pB = f.partB + (size_t)g * f.LB;
-
-    Ring rg;
-    rg.S = f.tma_stages;
     const bool two = f.dot_groups == 2;
     const int ring_ppr = two ? 1 : PPR;
-    rg.stage_floats = ring_ppr * N * 4;
-    rg.base = reinterpret_cast<float*>(dyn_smem);
-    rg.mbar = sm.mbar;
-    rg.issued = rg.used = 0;
     // reduced pass partials: this CTA's N-slice, then the k-vector (b' or the Gram row)
-    float* rb = reinterpret_cast<float*>(dyn_smem + (size_t)rg.S * rg.stage_floats * sizeof(float));
+    float* rb = reinterpret_cast<float*>(dyn_smem + f.ring_bytes);
     float* ka = rb + f.max_slice + f.ldk;
     const int nc1 = n1 - n0;
     float* sv = rb;
     float* kb = rb + nc1;
     auto slice_then_k = [&](int v) { return v < nc1 ? n0 + v : N + (v - nc1); };
     auto ident = [](int v) { return v; };
-
-    if (tid == 0) {
-        for (int s = 0; s < rg.S; ++s) mbar_init(reinterpret_cast<uint64_t*>(&sm.mbar[s]), 1);
-        fence_mbar_init();
-    }
-#ifdef GSPCA_PHASE_TIMING
-    if (g == 0 && tid == 0) {
-        for (int i = 0; i < 16; ++i) sm.tacc[i] = 0;
-        sm.tlast = globaltimer_ns();
-        sm.tcur = 0;
-    }
-#endif
-    // ||X||_F^2 from the pack kernel's partials (fixed order, every CTA).
-    if (warp == 0) {
-        double t = 0.0;
-        for (int i = lane; i < f.nxpart; i += 32) t += f.xpart[i];
-        t = warp_sum(t);
-        if (lane == 0) sm.dsc[0] = t;
-    }
-    __syncthreads();
-    const float threshf = (float)(f.eps_thresh * sqrt(sm.dsc[0]));
     const float tolf = (float)f.tol;
+    (void)warp;
+    (void)lane;
 
-    unsigned epoch = 0;
     int status = kStOK, found = K;
     long long total = 0;
     double lam_prev = 0.0;  // lambda of the last finished component
@@ -725,12 +1097,12 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
     ff sc;
     bool alive = true;
 
-#define GS_SYNC()                          \
-    do {                                   \
-        if (!bar.sync(epoch, &sm.flag)) {  \
-            alive = false;                 \
-            goto leave;                    \
-        }                                  \
+#define GS_SYNC()                         \
+    do {                                  \
+        if (!tm.sync(epoch, &sm.flag)) {  \
+            alive = false;                \
+            goto leave;                   \
+        }                                 \
     } while (0)
 
     for (int k = 0; k < K && found == K; ++k) {
@@ -744,13 +1116,19 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
             const int c = tid + i * T;
             uc[i] = (defl && c < N) ? ldcg(f.ut + (size_t)buf * N + c) * inv_nu : 0.f;
         }
-        row_pass<CPT, kPassCol>(f, sm, rg, p0, p1, uc, k, defl, lamf, k - 1, sacc, sc);
+        if (!row_pass<CPT, kPassCol>(f, sm, rg, p0, p1, uc, k, defl, lamf, k - 1, sacc, sc)) {
+            if (tm.fail(f)) {
+                alive = false;
+                goto leave;
+            }
+            sc = ff{__int_as_float(0x7fc00000), 0.f};
+        }
 #pragma unroll
         for (int i = 0; i < CPT; ++i) {
             const int c = tid + i * T;
             if (c < N) pA[c] = sacc[i];
         }
-        write_scalar(f, 0, sc);
+        write_scalar(f, g, 0, sc);
         if (gs && k > 0)  // Gram row (V^T v_{k-1})_j over this CTA's rows
             rows_times_matrix(f.V, f.ldv, r0, r1, k, [&](int r) { return f.V[(size_t)r * f.ldv + (k - 1)]; },
                               pA + N, sm);
@@ -759,18 +1137,21 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
 
         const bool small_k = k <= f.redundant_max;  // k-vectors reduced by every CTA
         const int nk0 = (gs && k > 0 && small_k) ? k : 0;
-        gather_reduce(f, sm, 1, 0, 0, f.partA, f.LA, nc1 + nk0, slice_then_k, rb);
+        gather_reduce(f, sm, G, 1, 0, 0, f.partA, f.LA, nc1 + nk0, slice_then_k, rb);
         if (sm.sff[0].hi == 0.f && sm.sff[0].lo == 0.f) {
             // Zero start column: restart from the residual column of largest
             // norm (lowest index on ties); every column zero => rank exhausted.
-            row_pass<CPT, kPassSq>(f, sm, rg, p0, p1, uc, 0, false, 0.f, 0, sacc, sc);
+            if (!row_pass<CPT, kPassSq>(f, sm, rg, p0, p1, uc, 0, false, 0.f, 0, sacc, sc) && tm.fail(f)) {
+                alive = false;
+                goto leave;
+            }
 #pragma unroll
             for (int i = 0; i < CPT; ++i) {
                 const int c = tid + i * T;
                 if (c < N) pA[c] = sacc[i];
             }
             GS_SYNC();
-            reduce_cols_distributed(f.partA, f.LA, 0, N, f.red);
+            reduce_cols_distributed(f.partA, G, g, f.LA, 0, N, f.red);
             GS_SYNC();
             if (warp == 0) {
                 double best = 0.0;
@@ -800,15 +1181,21 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
                 status = kStDegenerate;
                 break;
             }
-            row_pass<CPT, kPassCol>(f, sm, rg, p0, p1, uc, kcol, false, 0.f, 0, sacc, sc);
+            if (!row_pass<CPT, kPassCol>(f, sm, rg, p0, p1, uc, kcol, false, 0.f, 0, sacc, sc)) {
+                if (tm.fail(f)) {
+                    alive = false;
+                    goto leave;
+                }
+                sc = ff{__int_as_float(0x7fc00000), 0.f};
+            }
 #pragma unroll
             for (int i = 0; i < CPT; ++i) {
                 const int c = tid + i * T;
                 if (c < N) pA[c] = sacc[i];
             }
-            write_scalar(f, 0, sc);
+            write_scalar(f, g, 0, sc);
             GS_SYNC();
-            gather_reduce(f, sm, 1, 0, 0, f.partA, f.LA, nc1 + nk0, slice_then_k, rb);
+            gather_reduce(f, sm, G, 1, 0, 0, f.partA, f.LA, nc1 + nk0, slice_then_k, rb);
         }
         // ||x||^2 rescales the new loading so that its norm stays O(1).
         const float xx_inv = __fdiv_rn(1.f, __fadd_rn(sm.sff[0].hi, sm.sff[0].lo));
@@ -818,7 +1205,7 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
             // Gram row -> kb; then W <- R_k^T V for the deflation of component k-1:
             // W(:, j) -= lambda u (v_{k-1}.v_j), new column R_{k-1}^T v_{k-1} - lambda u |v_{k-1}|^2
             if (!small_k) {
-                reduce_cols_distributed(f.partA, f.LA, N, k, f.red);
+                reduce_cols_distributed(f.partA, G, g, f.LA, N, k, f.red);
                 GS_SYNC();
                 for (int j = tid; j < k; j += T) kb[j] = (float)ldcg(f.red + j);
                 __syncthreads();
@@ -843,9 +1230,9 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
             rows_times_matrix(f.U, f.ldu, n0, n1, k, [&](int n) { return sv[n - n0]; }, pB, sm);
             GS_SYNC();
             if (small_k) {
-                gather_reduce(f, sm, 0, 0, 0, f.partB, f.LB, k, ident, ka);
+                gather_reduce(f, sm, G, 0, 0, 0, f.partB, f.LB, k, ident, ka);
             } else {
-                reduce_cols_distributed(f.partB, f.LB, 0, k, f.red);
+                reduce_cols_distributed(f.partB, G, g, f.LB, 0, k, f.red);
                 GS_SYNC();
                 for (int j = tid; j < k; j += T) ka[j] = (float)ldcg(f.red + j);
                 __syncthreads();
@@ -865,7 +1252,7 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
             }
         }
         nq = block_sum_ff(nq, sm);
-        write_scalar(f, 2 + nb, nq);
+        write_scalar(f, g, 2 + nb, nq);
         buf = nb;
         ring_prefetch(f, rg, p0, p1, ring_ppr);
         GS_SYNC();
@@ -876,8 +1263,15 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
         for (;;) {
             PHASE_MARK(1);
             bool pass_ok = true, two_done = false;
+            if constexpr (CPT <= 2) {
+                if (f.narrow) {
+                    PHASE_MARK(2);
+                    pass_ok = pass_narrow<CPT>(f, sm, p0, p1, f.ut + (size_t)buf * N, pA, sc, dyn_smem);
+                    two_done = true;
+                }
+            }
             if constexpr (CPT <= 4) {
-                if (two) {
+                if (two && !two_done) {
                     float uc2[2 * CPT], sacc2[2 * CPT];
 #pragma unroll
                     for (int i = 0; i < 2 * CPT; ++i) {
@@ -910,11 +1304,13 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
                 }
             }
             if (!pass_ok) {
-                if (tid == 0) atomicCAS(f.abort, 0, kStTimeout);
-                alive = false;
-                goto leave;
+                if (tm.fail(f)) {
+                    alive = false;
+                    goto leave;
+                }
+                sc = ff{__int_as_float(0x7fc00000), 0.f};
             }
-            write_scalar(f, 0, sc);
+            write_scalar(f, g, 0, sc);
             if (gs && k > 0)  // b' = V_(k)^T v' over this CTA's rows
                 rows_times_matrix(f.V, f.ldv, r0, r1, k, [&](int r) { return f.vraw[r]; }, pA + N, sm);
             PHASE_MARK(3);
@@ -924,7 +1320,7 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
             ++total;
             const bool small_k = k <= f.redundant_max;
             // sff[0] = ||u'||^2 (pass input), sff[1] = ||v'||^2; this CTA's slice of s' (+ b')
-            gather_reduce(f, sm, 2, 2 + buf, 0, f.partA, f.LA, nc1 + ((gs && k > 0 && small_k) ? k : 0),
+            gather_reduce(f, sm, G, 2, 2 + buf, 0, f.partA, f.LA, nc1 + ((gs && k > 0 && small_k) ? k : 0),
                           slice_then_k, rb);
             const ff nu2 = sm.sff[0];
             const ff nvp = sm.sff[1];
@@ -944,7 +1340,7 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
                 // b' -> kb; v_corr' = v' - V b' (rows); u_pre' = s' - W b' (slice);
                 // a' = U^T u_pre' (partials)
                 if (!small_k) {
-                    reduce_cols_distributed(f.partA, f.LA, N, k, f.red);
+                    reduce_cols_distributed(f.partA, G, g, f.LA, N, k, f.red);
                     GS_SYNC();
                     for (int jj = tid; jj < k; jj += T) kb[jj] = (float)ldcg(f.red + jj);
                     __syncthreads();
@@ -964,14 +1360,14 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
                 __syncthreads();
                 rows_times_matrix(f.U, f.ldu, n0, n1, k, [&](int n) { return f.upre[n]; }, pB, sm);
                 l2 = block_sum_ff(l2, sm);
-                write_scalar(f, 1, l2);
+                write_scalar(f, g, 1, l2);
                 PHASE_MARK(7);
                 GS_SYNC();
                 PHASE_MARK(8);
-                gather_reduce(f, sm, 1, 1, 0, f.partB, f.LB, small_k ? k : 0, ident, ka);
+                gather_reduce(f, sm, G, 1, 1, 0, f.partB, f.LB, small_k ? k : 0, ident, ka);
                 lam2p = sm.sff[0];
                 if (!small_k) {
-                    reduce_cols_distributed(f.partB, f.LB, 0, k, f.red);
+                    reduce_cols_distributed(f.partB, G, g, f.LB, 0, k, f.red);
                     GS_SYNC();
                     for (int jj = tid; jj < k; jj += T) ka[jj] = (float)ldcg(f.red + jj);
                     __syncthreads();
@@ -1043,7 +1439,7 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
                 break;
             }
             mu = lamff;
-            write_scalar(f, 2 + nbuf, nq2);
+            write_scalar(f, g, 2 + nbuf, nq2);
             buf = nbuf;
             ring_prefetch(f, rg, p0, p1, ring_ppr);
             PHASE_MARK(11);
@@ -1053,16 +1449,50 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
 #undef GS_SYNC
 leave:
     if (!alive) ring_drain(f, rg);
+    return FitOutcome{status, found, total, alive};
+}
+
+// ------------------------------------------------------------------ kernels
+
+// Single problem, whole grid (cooperative launch).
+template <int CPT>
+__global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
+    __shared__ SmemFit sm;
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const TeamGrid tm{(int)gridDim.x, (int)blockIdx.x, GridBarrier{f.flags, f.abort, f.timeout_ns}};
+    if (tid == 0) sm.mbar_live = 0;
+#ifdef GSPCA_PHASE_TIMING
+    if (tid == 0) {
+        for (int i = 0; i < 16; ++i) sm.tacc[i] = 0;
+        sm.tlast = globaltimer_ns();
+        sm.tcur = 0;
+        sm.tmark = blockIdx.x == 0;
+    }
+#endif
+    // ||X||_F^2 from the pack kernel's partials (fixed order, every CTA).
+    if (warp == 0) {
+        double t = 0.0;
+        for (int i = lane; i < f.nxpart; i += 32) t += f.xpart[i];
+        t = warp_sum(t);
+        if (lane == 0) sm.dsc[0] = t;
+    }
+    __syncthreads();
+    const float threshf = (float)(f.eps_thresh * sqrt(sm.dsc[0]));
+    Ring rg;
+    ring_setup(rg, sm, dyn_smem, f.tma_stages, f.dot_groups == 2 ? 1 : PassShape<CPT>::PPR, f.N);
+    unsigned epoch = 0;
+    const FitOutcome r = fit_one<CPT>(f, tm, sm, dyn_smem, rg, threshf, epoch);
 #ifdef GSPCA_PHASE_TIMING
     PHASE_MARK(15);
-    if (g == 0 && tid == 0 && f.timing)
+    if (blockIdx.x == 0 && tid == 0 && f.timing)
         for (int i = 0; i < 16; ++i) f.timing[i] = sm.tacc[i];
 #endif
-    if (alive && g == 0 && tid == 0) {
-        f.info[kInfoStatus] = status;
-        f.info[kInfoFound] = found;
-        f.info[kInfoItersLo] = (int)(total & 0x7fffffff);
-        f.info[kInfoItersHi] = (int)(total >> 31);
+    if (r.alive && blockIdx.x == 0 && tid == 0) {
+        f.info[kInfoStatus] = r.status;
+        f.info[kInfoFound] = r.found;
+        f.info[kInfoItersLo] = (int)(r.total & 0x7fffffff);
+        f.info[kInfoItersHi] = (int)(r.total >> 31);
     }
 }
 

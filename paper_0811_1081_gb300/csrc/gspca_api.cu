@@ -10,6 +10,7 @@
 #include <new>
 
 #include "../../include/gspca.h"
+#include "handle.h"
 #include "launch_common.cuh"
 
 using namespace gspca;
@@ -21,36 +22,13 @@ char g_cuda_err[256] = "no CUDA error";
 unsigned long long* g_timing_dev = nullptr;  // instrumented builds only
 #endif
 
-bool cuda_ok(cudaError_t e) {
+}  // namespace
+
+bool gspca::cuda_ok(cudaError_t e) {
     if (e == cudaSuccess) return true;
     std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
     return false;
 }
-
-#define GS_CUDA(call)                              \
-    do {                                           \
-        if (!cuda_ok(call)) return GSPCA_ERR_CUDA; \
-    } while (0)
-
-}  // namespace
-
-struct gspca_handle {
-    int device = 0;
-    long max_M = 0, max_N = 0;
-    int max_K = 0;
-    gspca_dtype dtype = GSPCA_F32;
-    int num_sms = 0;
-    void* ws_base = nullptr;
-    Workspace ws{};
-    int* h_info = nullptr;                     // pinned
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the persistent kernel
-    // host-buffer entry point staging (allocated on first use)
-    void* stage = nullptr;
-    float *sX = nullptr, *sT = nullptr, *sP = nullptr, *sR = nullptr;
-    double* slam = nullptr;
-    int* siters = nullptr;
-    gspca_info last{};
-};
 
 namespace {
 
@@ -70,7 +48,8 @@ gspca_status check_fit_args(gspca_t h, const void* X, gspca_layout layout, long 
         return GSPCA_ERR_INVALID_ARG;
     }
     if (opts) {
-        if (opts->center < 0 || opts->center > 2 || opts->grid_ctas < 0 || opts->timeout_s < 0)
+        if (opts->center < 0 || opts->center > 2 || opts->grid_ctas < 0 || opts->timeout_s < 0 ||
+            opts->test_stall < 0 || opts->test_stall > 1)
             return GSPCA_ERR_INVALID_ARG;
         if (opts->iters_lock)
             for (int k = 0; k < K; ++k)
@@ -97,6 +76,7 @@ gspca_status enqueue_fit(gspca_t h, cudaStream_t s, const float* X, gspca_layout
         lock_dev = h->ws.lock;
     }
     FitArgs a = make_args(h->ws, plan, M, N, K, tol, max_iter, algo, lock_dev, timeout, nxpart);
+    if (opts && opts->test_stall) a.stall_word = h->ws.abort + 2;  // a word nothing sets
 #ifdef GSPCA_PHASE_TIMING
     if (!g_timing_dev) cudaMalloc(&g_timing_dev, 16 * sizeof(unsigned long long));
     cudaMemsetAsync(g_timing_dev, 0, 16 * sizeof(unsigned long long), s);
@@ -106,6 +86,8 @@ gspca_status enqueue_fit(gspca_t h, cudaStream_t s, const float* X, gspca_layout
     GS_CUDA(enqueue_sequence(h->ws, plan, a, s, X, layout, ldx, center, T, P, lambda, iters, R_out, h->ev0, h->ev1,
                              &launches));
     h->last.grid_ctas = plan.G;
+    h->last.team_ctas = plan.G;
+    h->last.batch_pass = 0;
     h->last.block_threads = kBlock;
     h->last.kernel_launches = launches;
     return GSPCA_OK;
@@ -264,15 +246,6 @@ gspca_status gspca_fit_host(gspca_t h, void* stream, const float* X, gspca_layou
     return finish(h, s, K, algo, M, N);
 }
 
-gspca_status gspca_fit_batched(gspca_t h, void* stream, const gspca_problem* problems, int count, double tol,
-                               int max_iter, gspca_algo algo, const gspca_opts* opts) {
-    (void)stream;
-    (void)opts;
-    if (!h || !problems || count < 1 || !(tol > 0.0) || max_iter < 1) return GSPCA_ERR_INVALID_ARG;
-    if (algo != GSPCA_NIPALS && algo != GSPCA_GS) return GSPCA_ERR_INVALID_ARG;
-    return GSPCA_ERR_NOT_SUPPORTED;
-}
-
 gspca_status gspca_get_info(gspca_t h, gspca_info* info) {
     if (!h || !info) return GSPCA_ERR_INVALID_ARG;
     *info = h->last;
@@ -288,6 +261,7 @@ gspca_status gspca_destroy(gspca_t h) {
     if (h->h_info && !cuda_ok(cudaFreeHost(h->h_info))) st = GSPCA_ERR_CUDA;
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
+    batch_release(h->batch);
     delete h;
     return st;
 }

@@ -11,76 +11,12 @@
 #include "../../include/gspca.h"
 #include "fit_kernel.cuh"
 #include "prep_kernels.cuh"
+#include "workspace.cuh"
 
 namespace gspca {
 
 constexpr int kMaxCols = 16 * kBlock;   // columns one CTA holds (CPT <= 16)
 constexpr int kRedundantMax = 128;      // k up to which every CTA reduces a k-vector itself
-
-inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-// Dimensions the workspace is laid out for (maximum sizes for a handle, the
-// exact problem for the no-allocation entry point).
-struct WsDims {
-    long Mp;   // rows rounded up to a multiple of 4
-    int N, K;
-    int G;     // CTAs the partial buffers hold
-};
-
-inline int ws_ld(int K) { return (int)align_up((size_t)K, 4); }
-inline int ws_LA(int N, int K) { return (int)align_up((size_t)N + K + 4, 4); }
-inline int ws_xcap(long Mp, int N) { return (int)(((N + 31) / 32) * ((Mp / 4 + 31) / 32)); }
-
-struct Workspace {
-    float *R, *V, *U, *W, *vraw, *vcorr, *ut, *upre, *partA, *partB;
-    float2* spart;
-    double *red, *lam, *xpart, *cmean, *rmean;
-    int *iters, *info, *abort, *lock;
-    unsigned* flags;
-    int ld, LA, LB, G, xcap;
-    size_t bytes;
-};
-
-// Lay the workspace out from `base` (nullptr: only compute the size).
-inline Workspace carve(void* base, const WsDims& d) {
-    Workspace w{};
-    w.ld = ws_ld(d.K);
-    w.LA = ws_LA(d.N, d.K);
-    w.LB = w.ld;
-    w.G = d.G;
-    w.xcap = ws_xcap(d.Mp, d.N);
-    char* b = static_cast<char*>(base);
-    size_t off = 0;
-    auto take = [&](size_t bytes) -> void* {
-        off = align_up(off, 256);
-        void* p = b ? b + off : nullptr;
-        off += align_up(bytes > 0 ? bytes : 1, 256);
-        return p;
-    };
-    w.R = (float*)take(sizeof(float) * (size_t)d.Mp * d.N);
-    w.V = (float*)take(sizeof(float) * (size_t)d.Mp * w.ld);
-    w.U = (float*)take(sizeof(float) * (size_t)d.N * w.ld);
-    w.W = (float*)take(sizeof(float) * (size_t)d.N * w.ld);
-    w.vraw = (float*)take(sizeof(float) * (size_t)d.Mp);
-    w.vcorr = (float*)take(sizeof(float) * (size_t)d.Mp);
-    w.ut = (float*)take(sizeof(float) * 2 * (size_t)d.N);
-    w.upre = (float*)take(sizeof(float) * (size_t)d.N);
-    w.partA = (float*)take(sizeof(float) * (size_t)d.G * w.LA);
-    w.partB = (float*)take(sizeof(float) * (size_t)d.G * w.LB);
-    w.spart = (float2*)take(sizeof(float2) * 4 * (size_t)d.G);
-    w.red = (double*)take(sizeof(double) * (size_t)w.LA);
-    w.lam = (double*)take(sizeof(double) * (size_t)d.K);
-    w.xpart = (double*)take(sizeof(double) * (size_t)w.xcap);
-    w.cmean = (double*)take(sizeof(double) * (size_t)d.N);
-    w.rmean = (double*)take(sizeof(double) * (size_t)d.Mp);
-    w.iters = (int*)take(sizeof(int) * (size_t)d.K);
-    w.info = (int*)take(sizeof(int) * kInfoWords);
-    w.abort = (int*)take(sizeof(int) * 4);
-    w.lock = (int*)take(sizeof(int) * (size_t)d.K);
-    w.flags = (unsigned*)take(sizeof(unsigned) * 32);
-    w.bytes = off;
-    return w;
-}
 
 struct Plan {
     int cpt, ppr, G, S, ldk, max_slice, groups;
@@ -218,6 +154,7 @@ inline FitArgs make_args(const Workspace& w, const Plan& p, int M, int N, int K,
     a.timing = nullptr;
     a.tma_stages = p.S;
     a.dot_groups = p.groups;
+    a.ring_bytes = (int)(p.dyn - sizeof(float) * (2 * (size_t)p.ldk + p.max_slice));
     a.ldk = p.ldk;
     a.max_slice = p.max_slice;
     a.redundant_max = kRedundantMax;

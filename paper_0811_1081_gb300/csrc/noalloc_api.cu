@@ -56,7 +56,8 @@ extern "C" gspca_status gspca_fit_noalloc(void* stream, const float* X, gspca_la
         (layout != GSPCA_COL_MAJOR && layout != GSPCA_ROW_MAJOR))
         return GSPCA_ERR_INVALID_ARG;
     if (opts) {
-        if (opts->center < 0 || opts->center > 2 || opts->grid_ctas < 0 || opts->timeout_s < 0)
+        if (opts->center < 0 || opts->center > 2 || opts->grid_ctas < 0 || opts->timeout_s < 0 ||
+            opts->test_stall < 0 || opts->test_stall > 1)
             return GSPCA_ERR_INVALID_ARG;
         if (opts->iters_lock)
             for (int k = 0; k < K; ++k)
@@ -89,7 +90,8 @@ extern "C" gspca_status gspca_fit_noalloc(void* stream, const float* X, gspca_la
         lock_dev = w.lock;
     }
     const double timeout = (opts && opts->timeout_s > 0) ? opts->timeout_s : 2.0;
-    const FitArgs a = make_args(w, plan, M, N, K, tol, max_iter, algo, lock_dev, timeout, nxpart);
+    FitArgs a = make_args(w, plan, M, N, K, tol, max_iter, algo, lock_dev, timeout, nxpart);
+    if (opts && opts->test_stall) a.stall_word = w.abort + 2;  // a word nothing sets
     int launches = 0;
     // the pack kernel, first in the sequence, clears the barrier, abort and status words
     if (enqueue_sequence(w, plan, a, s, X, layout, ldx, opts ? opts->center : 0, T, P, lambda, iters, R_out,

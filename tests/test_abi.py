@@ -71,3 +71,32 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     with pytest.raises(RuntimeError):
         gp.load()
     importlib.reload(b)
+
+
+def header_struct_fields(name):
+    """Field names, in order, of `typedef struct { ... } name;` in gspca.h."""
+    src = open(os.path.join(ROOT, "include", "gspca.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    bodies = {n: b for b, n in re.findall(r"typedef struct\s*\{([^{}]*)\}\s*(\w+)\s*;", src)}
+    assert name in bodies, name
+    fields = []
+    for decl in bodies[name].split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        # "int M, N, K" / "float *T, *P" / "const int *iters_lock"
+        head, *rest = decl.split(",")
+        names = [re.findall(r"(\w+)\s*$", head)[0]] + [re.findall(r"(\w+)\s*$", r)[0] for r in rest]
+        fields += names
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("gspca_opts", "Opts"), ("gspca_info", "Info"),
+                                          ("gspca_problem", "Problem")])
+def test_ctypes_structs_match_header(cname, pyname):
+    """The binding's ctypes structures list the header's fields in the header's order."""
+    import paper_0811_1081_gb300 as gp
+
+    want = header_struct_fields(cname)
+    got = [f.rstrip("_") for f, _ in getattr(gp, pyname)._fields_]
+    assert got == want, (cname, got, want)
