@@ -39,6 +39,48 @@ UNIT = "components/s"
 FALLBACK_HBM_GBS = 6800.0
 
 
+def kernel_name(N):
+    """The instantiation of the persistent fit kernel for N columns (columns per thread)."""
+    cpt = 1
+    while cpt * 512 < N:
+        cpt *= 2
+    return f"fit_kernel<{cpt}>"
+
+
+def source_sha():
+    """SHA-256 over the CUDA sources, to tell whether profile counters still apply."""
+    import hashlib
+
+    d = os.path.join(ROOT, "paper_0811_1081_gb300", "csrc")
+    hsh = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, name), "rb") as f:
+                hsh.update(name.encode() + b"\0" + f.read())
+    return hsh.hexdigest()
+
+
+def profiled_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary
+    (profiles/<kernel>_<workload>.md), or None when it is absent or was taken on other sources."""
+    name = kernel.replace("<", "_").replace(">", "")
+    p = os.path.join(ROOT, "profiles", f"{name}_{workload}.md")
+    if not os.path.exists(p):
+        return None, None
+    vals = {}
+    with open(p) as f:
+        for ln in f:
+            if ":" in ln and ln.strip().startswith("- "):
+                k, v = ln.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha256") != source_sha():
+        return None, p
+    try:
+        return float(vals["dram_bytes_per_launch"]), p
+    except (KeyError, ValueError):
+        return None, p
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -180,6 +222,57 @@ def config(w, args, l2):
             "max_iter": w.max_iter, "storage": "f32", "l2": l2, "parallelism": "replicas"}
 
 
+def bench_batched(gp, dev, args):
+    """Secondary measurement: the 256-problem workload (M log-uniform in [256, 8192], N in
+    [64, 1024], K = 16, planted spectra 10 * 0.9^i, noise 0.01, tol 1e-6) as one batched
+    launch (team size and pass from the autotuner) and as plain per-problem gspca_fit calls,
+    both FP32 and device-timed with CUDA events; L2 flushed before each timed run."""
+    import torch
+
+    shapes = synth.batch_shapes()
+    K = 16
+    probs = [torch.from_numpy(synth.batch_problem(i, M, N).X.astype(np.float32)).to(dev)
+             for i, (M, N) in enumerate(shapes)]
+    batch = gp.Batch([{"X": X.t().contiguous().t(), "K": K} for X in probs])
+    h = gp.Handle(max(m for m, _ in shapes), max(n for _, n in shapes), K, device=dev.index or 0)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    gp.gspca_fit_batched(h.h, batch)  # autotunes
+    reps = 3
+    b_ms, b_bytes, b_found, b_iters = [], [], 0, 0
+    for i in range(reps):
+        flush.fill_(float(i))
+        _, st = gp.gspca_fit_batched(h.h, batch)
+        info = h.info()
+        b_ms.append(info["kernel_ms"])
+        b_bytes.append(info["alg_bytes"])
+        b_found, b_iters = info["found"], info["total_iters"]
+    team, bpass = info["team_ctas"], info["batch_pass"]
+    # plain per-problem form: one gspca_fit per problem, back to back on the stream
+    stream = torch.cuda.current_stream(dev)
+    for X in probs[:4]:
+        h.fit(X, K)
+    flush.fill_(0.0)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    p_found, p_iters = 0, 0
+    for X in probs:
+        r = h.fit(X, K)
+        p_found += r.info["found"]
+        p_iters += r.info["total_iters"]
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    p_ms = a.elapsed_time(b)
+    h.close()
+    bm = min(b_ms)
+    return {"workload": "256 planted problems, M in [256, 8192], N in [64, 1024] (log-uniform), K=16",
+            "value": b_found / bm * 1e3, "unit": UNIT, "ms": bm, "team_ctas": team, "pass": bpass,
+            "alg_gbs": b_bytes[b_ms.index(bm)] / bm / 1e6, "iters_total": b_iters,
+            "status": gp.status_string(st),
+            "plain_per_problem": {"value": p_found / p_ms * 1e3, "unit": UNIT, "ms": p_ms,
+                                  "iters_total": p_iters},
+            "speedup_vs_plain": (b_found / bm) / (p_found / p_ms)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -191,6 +284,8 @@ def main():
     ap.add_argument("--ref-components", type=int, default=2)
     ap.add_argument("--cpu-components", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the secondary 256-problem batched measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -244,6 +339,10 @@ def main():
 
     # roofline of the persistent kernel: algorithmic bytes / its event-timed duration
     peak, peak_src = measured_peaks()
+    kname = kernel_name(N)
+    traffic, traffic_src = profiled_traffic(kname, w.name)
+    if traffic_src:
+        traffic_src = os.path.relpath(traffic_src, ROOT) + (" (sources changed since: null)" if traffic is None else "")
     k_s = sum(kern_ms) / 1e3
     achieved = sum(alg_bytes) / k_s / 1e9
     kernel_share = sum(kern_ms) / sum(step_ms)
@@ -279,7 +378,8 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "fit_kernel<4>",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": kname,
+                     "traffic_source": traffic_src,
                      "peak_source": peak_src, "kernel_share_of_step": kernel_share,
                      "kernel_ms_mean": statistics.mean(kern_ms),
                      "alg_bytes_per_launch": statistics.mean(alg_bytes)},
@@ -288,6 +388,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms)},
     }
+    if not args.no_batched:
+        line["batched"] = bench_batched(gp, dev, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         X64 = X32.astype(np.float64)
         dt, f = cpu_oracle_sample(X64, w, args.algo, args.cpu_components)

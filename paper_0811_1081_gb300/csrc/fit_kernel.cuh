@@ -706,7 +706,13 @@ __device__ __forceinline__ bool pass_narrow(const FitArgs& f, SmemFit& sm, int p
 // a lane issues kVecRows such loads before using any of them.
 constexpr int kVecRows = 8;
 
-__device__ __forceinline__ bool vec_lda(int lda) { return lda >= 4 && lda <= 128 && (lda & (lda - 1)) == 0; }
+// Used for long row ranges only: with few rows per CTA, spreading rows over
+// all warps (the general path) finishes sooner than packing them into few.
+constexpr int kVecMinRows = 512;
+
+__device__ __forceinline__ bool vec_rows(int lda, int rows) {
+    return rows >= kVecMinRows && lda >= 4 && lda <= 128 && (lda & (lda - 1)) == 0;
+}
 
 template <class Y>
 __device__ __forceinline__ void rows_times_matrix_vec(const float* A, int lda, int r0, int r1, int kk, Y y,
@@ -790,7 +796,7 @@ __device__ __forceinline__ void matrix_times_vector_vec(const float* A, int lda,
 template <class Y>
 __device__ __forceinline__ void rows_times_matrix(const float* A, int lda, int r0, int r1, int kk, Y y, float* dst,
                                                   SmemFit& sm) {
-    if (vec_lda(lda)) {
+    if (vec_rows(lda, r1 - r0)) {
         rows_times_matrix_vec(A, lda, r0, r1, kk, y, dst, sm);
         return;
     }
@@ -836,7 +842,7 @@ __device__ __forceinline__ void rows_times_matrix(const float* A, int lda, int r
 template <class Pre, class Fn>
 __device__ __forceinline__ void matrix_times_vector(const float* A, int lda, int r0, int r1, int kk, const float* x,
                                                     Pre pre, Fn fn) {
-    if (vec_lda(lda)) {
+    if (vec_rows(lda, r1 - r0)) {
         matrix_times_vector_vec(A, lda, r0, r1, kk, x, pre, fn);
         return;
     }
