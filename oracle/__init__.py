@@ -47,8 +47,10 @@ def _load():
             dp = ctypes.POINTER(ctypes.c_double)
             ip = ctypes.POINTER(ctypes.c_int)
             lib.oracle_fit.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, ip,
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int,
                                        dp, dp, dp, ip, dp, ip]
+            lib.oracle_round_bf16.argtypes = [ctypes.c_double]
+            lib.oracle_round_bf16.restype = ctypes.c_double
             lib.oracle_fit.restype = ctypes.c_int
             lib.oracle_center.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.oracle_center.restype = ctypes.c_int
@@ -80,9 +82,15 @@ class Fit:
     status: int          # 0 ok, 4 not converged, 5 degenerate
 
 
+STORAGE = {"f64": 0, "bf16": 1}
+
+
 def fit(X: np.ndarray, K: int, tol: float = 1e-6, max_iter: int = 1000, algo: int | str = GS,
-        center: int = CENTER_NONE, iters_lock=None) -> Fit:
-    """Run NIPALS-PCA (algo=0/'nipals') or GS-PCA (algo=1/'gs') on X (M×N) in FP64."""
+        center: int = CENTER_NONE, iters_lock=None, storage: str = "f64") -> Fit:
+    """Run NIPALS-PCA (algo=0/'nipals') or GS-PCA (algo=1/'gs') on X (M×N) in FP64.
+
+    storage="bf16": the residual R is rounded to bfloat16 after centring and after
+    every deflation (Eq. 3); all arithmetic stays FP64."""
     if isinstance(algo, str):
         algo = {"nipals": NIPALS, "gs": GS}[algo.lower()]
     X = np.asfortranarray(np.asarray(X, dtype=np.float64))
@@ -99,11 +107,18 @@ def fit(X: np.ndarray, K: int, tol: float = 1e-6, max_iter: int = 1000, algo: in
         if lock.shape != (K,):
             raise ValueError("iters_lock must have K entries")
     st = _load().oracle_fit(algo, _dptr(X), M, N, K, float(tol), int(max_iter), int(center),
-                            _iptr(lock), _dptr(T), _dptr(P), _dptr(lam), _iptr(iters),
+                            _iptr(lock), STORAGE[storage], _dptr(T), _dptr(P), _dptr(lam), _iptr(iters),
                             _dptr(R), _iptr(found))
     if st == 1:
         raise ValueError("oracle_fit: invalid argument")
     return Fit(T=T, P=P, lam=lam, iters=iters, R=R, found=int(found[0]), status=int(st))
+
+
+def round_bf16(x) -> np.ndarray:
+    """Every entry of x rounded to the nearest bfloat16 (ties to even), as float64."""
+    lib = _load()
+    a = np.asarray(x, dtype=np.float64)
+    return np.vectorize(lib.oracle_round_bf16, otypes=[np.float64])(a) if a.size else a.copy()
 
 
 def center(X: np.ndarray, mode: int) -> np.ndarray:

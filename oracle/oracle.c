@@ -26,7 +26,12 @@
  *         ties); when every column is zero the fit stops as degenerate;
  *       * rank exhausted: a norm <= 64*eps64*||X||_F stops the fit as
  *         degenerate; the components found so far are kept, the rest are 0;
- *       * NIPALS returns lambda_k = ||t_k|| (the pseudo-code's lambda').
+ *       * NIPALS returns lambda_k = ||t_k|| (the pseudo-code's lambda');
+ *       * storage 1 ("R held in bfloat16", a precision variant of Sec. 3's
+ *         remark that the programs switch precision by their type alone): the
+ *         residual is rounded to the nearest bfloat16 after centring and after
+ *         every deflation (Eq. 3), and used exactly as stored; all arithmetic
+ *         on it stays FP64.
  *   - Status codes: 0 ok, 1 invalid argument, 4 at least one component hit
  *     max_iter, 5 degenerate (fewer than K components found).
  *
@@ -43,6 +48,38 @@
 #define OR_DEGENERATE 5
 
 /* ---------------------------------------------------------------- helpers */
+
+/* Largest finite bfloat16: (2 - 2^-7) * 2^127. */
+#define BF16_MAX (0x1.fep127)
+
+/* Round x to the nearest bfloat16 value, ties to even.  bfloat16 keeps the
+ * 8-bit exponent of IEEE binary32 and 8 significant bits (7 stored): for
+ * |x| in [2^(e-1), 2^e) with e-1 >= -126 the representable values are the
+ * multiples of 2^(e-8); below 2^-126 (subnormal) the multiples of 2^-133.
+ * Magnitudes that round beyond BF16_MAX become infinities. */
+double oracle_round_bf16(double x)
+{
+    if (x == 0.0 || !isfinite(x))
+        return x;
+    int e;
+    frexp(x, &e);
+    if (e < -125)
+        e = -125;
+    const double q = ldexp(1.0, e - 8);
+    const double r = nearbyint(x / q) * q; /* default rounding mode: to nearest, ties to even */
+    if (fabs(r) > BF16_MAX)
+        return copysign(INFINITY, x);
+    return r;
+}
+
+/* Apply the storage rounding of R (storage 1: bfloat16) to n values. */
+static void store_round(double *R, size_t n, int storage)
+{
+    if (storage != 1)
+        return;
+    for (size_t i = 0; i < n; i++)
+        R[i] = oracle_round_bf16(R[i]);
+}
 
 static double dot(const double *x, const double *y, int n)
 {
@@ -213,7 +250,7 @@ int oracle_center(double *R, int M, int N, int mode)
  *     R <- R - T(k) P(k)^T            (Eq. 3)
  * T keeps the unnormalised scores, so X = T P^T + R (Eq. 4). */
 static int nipals(double *R, int M, int N, int K, double tol, int max_iter,
-                  const int *iters_lock, double thresh,
+                  const int *iters_lock, double thresh, int storage,
                   double *T, double *P, double *lambda, int *iters, int *found)
 {
     int not_converged = 0;
@@ -253,6 +290,7 @@ static int nipals(double *R, int M, int N, int K, double tol, int max_iter,
         lambda[k] = cur;
         iters[k] = j;
         ger(R, M, N, -1.0, t, p);
+        store_round(R, (size_t)M * N, storage);
     }
     *found = K;
     return not_converged ? OR_NOT_CONVERGED : OR_OK;
@@ -275,7 +313,7 @@ static int nipals(double *R, int M, int N, int K, double tol, int max_iter,
  * While a component is being extracted, column j < k of T holds V(j) (unit
  * norm); the scaling T = V Lambda happens once at the end. */
 static int gspca(double *R, int M, int N, int K, double tol, int max_iter,
-                 const int *iters_lock, double thresh,
+                 const int *iters_lock, double thresh, int storage,
                  double *T, double *P, double *lambda, int *iters, int *found)
 {
     int not_converged = 0, status = OR_OK, kfound = K;
@@ -326,6 +364,7 @@ static int gspca(double *R, int M, int N, int K, double tol, int max_iter,
         lambda[k] = lam;
         iters[k] = j;
         ger(R, M, N, -lam, v, u);
+        store_round(R, (size_t)M * N, storage);
     }
     free(coef);
     for (int k = 0; k < kfound; k++)
@@ -344,10 +383,11 @@ static int gspca(double *R, int M, int N, int K, double tol, int max_iter,
  * final residual (X, centred as requested, minus every extracted component).
  * iters_lock (nullable): run exactly iters_lock[k] iterations for component k
  * and ignore the convergence test (used to replay another implementation's
- * iteration counts).  Outputs: T (M x K), P (N x K), lambda (K), iters (K),
- * found (number of components extracted). */
+ * iteration counts).  storage: 0 = R kept in FP64; 1 = R rounded to bfloat16
+ * after centring and after every deflation.  Outputs: T (M x K), P (N x K),
+ * lambda (K), iters (K), found (number of components extracted). */
 int oracle_fit(int algo, const double *X, int M, int N, int K, double tol, int max_iter,
-               int center, const int *iters_lock,
+               int center, const int *iters_lock, int storage,
                double *T, double *P, double *lambda, int *iters, double *R, int *found)
 {
     if (!X || !T || !P || !lambda || !iters || !R || !found)
@@ -355,6 +395,8 @@ int oracle_fit(int algo, const double *X, int M, int N, int K, double tol, int m
     if (M < 1 || N < 1 || K < 1 || K > M || K > N || !(tol > 0.0) || max_iter < 1)
         return OR_INVALID;
     if (algo != 0 && algo != 1)
+        return OR_INVALID;
+    if (storage != 0 && storage != 1)
         return OR_INVALID;
     if (iters_lock)
         for (int k = 0; k < K; k++)
@@ -364,10 +406,11 @@ int oracle_fit(int algo, const double *X, int M, int N, int K, double tol, int m
     int st = oracle_center(R, M, N, center);
     if (st != OR_OK)
         return st;
+    store_round(R, (size_t)M * N, storage);
     double thresh = 64.0 * DBL_EPSILON * frob(R, M, N);
     if (algo == 0)
-        return nipals(R, M, N, K, tol, max_iter, iters_lock, thresh, T, P, lambda, iters, found);
-    return gspca(R, M, N, K, tol, max_iter, iters_lock, thresh, T, P, lambda, iters, found);
+        return nipals(R, M, N, K, tol, max_iter, iters_lock, thresh, storage, T, P, lambda, iters, found);
+    return gspca(R, M, N, K, tol, max_iter, iters_lock, thresh, storage, T, P, lambda, iters, found);
 }
 
 /* ------------------------------------------------------- Jacobi eigensolver */

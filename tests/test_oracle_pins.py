@@ -290,3 +290,77 @@ def test_centering_modes(oracle_mod):
     f = oracle_mod.fit(X, 2, tol=1e-10, max_iter=1000, algo="gs", center=1)
     h = oracle_mod.fit(C1, 2, tol=1e-10, max_iter=1000, algo="gs")
     np.testing.assert_allclose(f.lam, h.lam, rtol=1e-14)
+
+
+# ------------------------------------------------------- bfloat16 storage of R
+
+def _bf16_by_bits(x32: np.ndarray) -> np.ndarray:
+    """Round-to-nearest-even float32 -> bfloat16 by integer arithmetic on the bit
+    pattern (add 0x7fff plus the lowest kept bit, drop the low 16 bits), widened back."""
+    b = np.ascontiguousarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+def test_round_bf16_against_bit_rounding_and_library(oracle_mod):
+    """oracle.round_bf16 agrees with two independent routes on float32 inputs (a single
+    rounding either way): the bit-pattern rule and torch's float32 -> bfloat16 cast; and
+    the halfway cases go to the even neighbour."""
+    g = synth.rng(31)
+    mags = 10.0 ** g.uniform(-42, 38, size=4000)
+    x = (np.where(g.random(4000) < 0.5, -1.0, 1.0) * mags).astype(np.float32)
+    x = x[np.isfinite(x)]
+    got = oracle_mod.round_bf16(x.astype(np.float64))
+    fin = np.abs(x.astype(np.float64)) < 3.38e38  # the bit rule does not saturate to inf
+    np.testing.assert_array_equal(got[fin], _bf16_by_bits(x[fin]))
+    torch = pytest.importorskip("torch")
+    lib = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(got, lib)
+    ties = oracle_mod.round_bf16(np.array([1 + 2.0**-8, 1 + 3 * 2.0**-8, -(1 + 2.0**-8), 2.0**-133 * 1.5,
+                                           2.0**-133 * 2.5, 0.0, 3.0]))
+    np.testing.assert_array_equal(ties, [1.0, 1 + 2.0**-6, -1.0, 2.0**-132, 2.0**-132, 0.0, 3.0])
+    big = oracle_mod.round_bf16(np.array([3.3961e38, 3.3962e38]))  # (2 - 2^-8) 2^127 = 3.39615e38
+    assert big[0] == float.fromhex("0x1.fep127") and np.isinf(big[1])
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_bf16_storage_rounds_every_residual(oracle_mod, algo):
+    """storage="bf16": the returned residual is made of bfloat16 values, and Eq. 4 holds up
+    to the rounding of the K deflations (each moves an entry by at most half a bfloat16
+    spacing, 2^-9 of its magnitude) but no better than a single rounding would allow."""
+    X = synth.planted(90, 50, 10.0, 0.85, 0.01, 44).X
+    K = 5
+    f = oracle_mod.fit(X, K, tol=1e-12, max_iter=5000, algo=algo, storage="bf16")
+    assert f.found == K
+    np.testing.assert_array_equal(oracle_mod.round_bf16(f.R), f.R)
+    Xb = oracle_mod.round_bf16(X)
+    err = np.linalg.norm(Xb - f.T @ f.P.T - f.R)
+    assert err <= K * 2.0**-9 * np.linalg.norm(Xb)
+    assert err >= 1e-5 * np.linalg.norm(f.R)
+    # the FP64 run on the same rounded input keeps Eq. 4 to rounding level: the gap is the storage
+    f64 = oracle_mod.fit(Xb, K, tol=1e-12, max_iter=5000, algo=algo)
+    assert np.linalg.norm(Xb - f64.T @ f64.P.T - f64.R) <= 1e-12 * np.linalg.norm(Xb)
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_bf16_storage_singular_values_within_weyl_bound(oracle_mod, algo):
+    """Rounding the residual after deflation j perturbs it by E_j with ||E_j||_2 <= ||E_j||_F
+    <= 2^-9 ||R_j||_F; by Weyl's inequality each singular value of the later residuals moves
+    by at most the sum of those, so converged lambdas of the bf16-storage run stay that close
+    to the FP64 run on the same rounded X (and do move: the rounding is applied)."""
+    X = synth.planted(120, 60, 10.0, 0.8, 0.01, 45).X
+    Xb = oracle_mod.round_bf16(X)
+    K = 6
+    fb = oracle_mod.fit(Xb, K, tol=1e-13, max_iter=20000, algo=algo, storage="bf16")
+    f64 = oracle_mod.fit(Xb, K, tol=1e-13, max_iter=20000, algo=algo)
+    bound = 0.0
+    moved = 0.0
+    for k in range(K):
+        # ||R_k||_F^2 = ||X||_F^2 - sum_{j<k} lambda_j^2 for the FP64 run (exact deflation of
+        # converged singular pairs); the bf16 bound uses its square root at every step
+        bound += 2.0**-9 * math.sqrt(max(0.0, np.sum(Xb**2) - np.sum(f64.lam[:k] ** 2)))
+        if k > 0:
+            assert abs(fb.lam[k] - f64.lam[k]) <= 1.5 * bound, (k, fb.lam[k], f64.lam[k], bound)
+        moved = max(moved, abs(fb.lam[k] - f64.lam[k]) / f64.lam[k])
+    assert abs(fb.lam[0] - f64.lam[0]) <= 1e-10 * f64.lam[0]  # component 0 sees no deflation
+    assert moved > 1e-9
