@@ -219,7 +219,7 @@ def run_reference(args):
 
 def config(w, args, l2):
     return {"workload": w.name, "M": w.M, "N": w.N, "K": w.K, "algo": args.algo, "tol": w.tol,
-            "max_iter": w.max_iter, "storage": "f32", "l2": l2, "parallelism": "replicas"}
+            "max_iter": w.max_iter, "storage": args.storage, "l2": l2, "parallelism": "replicas"}
 
 
 def bench_batched(gp, dev, args):
@@ -281,6 +281,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="planted_10000x2000")
     ap.add_argument("--algo", default="gs", choices=["gs", "nipals"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16"],
+                    help="storage type of the residual R inside the library")
     ap.add_argument("--ref-components", type=int, default=2)
     ap.add_argument("--cpu-components", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -305,7 +307,7 @@ def main():
     M, N, K = X32.shape[0], X32.shape[1], w.K
     Xd = torch.from_numpy(X32).to(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    h = gp.Handle(M, N, K, device=local)
+    h = gp.Handle(M, N, K, device=local, dtype=args.storage)
     stream = torch.cuda.current_stream(dev)
 
     for _ in range(args.warmup):

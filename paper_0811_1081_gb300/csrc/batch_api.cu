@@ -20,9 +20,15 @@ namespace {
 
 constexpr int kBatchMaxN = 2 * kBlock;  // columns per thread 1 or 2
 
-cudaError_t plan_batch(int device, int C, long maxM, int maxN, int maxK, BatchPlan* bp) {
+// The batched kernel for a storage type.
+const void* batch_kernel_for(gspca_dtype dt) {
+    return dt == GSPCA_BF16 ? batch_kernel_ptr<__nv_bfloat16>() : batch_kernel_ptr<float>();
+}
+
+cudaError_t plan_batch(int device, gspca_dtype dt, int C, long maxM, int maxN, int maxK, BatchPlan* bp) {
+    const void* kern = batch_kernel_for(dt);
     cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, batch_kernel);
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;
     int optin = 0;
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device)) != cudaSuccess)
@@ -38,11 +44,9 @@ cudaError_t plan_batch(int device, int C, long maxM, int maxN, int maxK, BatchPl
     if (ring < kLdsBytes) return cudaErrorInvalidConfiguration;  // the warp-group pass needs its stages
     bp->ring_bytes = (int)ring;
     bp->dyn = (size_t)dyn;
-    if ((e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bp->dyn)) !=
-        cudaSuccess)
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bp->dyn)) != cudaSuccess)
         return e;
-    if (C > 8 && (e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) !=
-                     cudaSuccess)
+    if (C > 8 && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
         return e;
     int sms = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
@@ -58,7 +62,7 @@ cudaError_t plan_batch(int device, int C, long maxM, int maxN, int maxK, BatchPl
     cfg.attrs = &at;
     cfg.numAttrs = 1;
     int n = 0;
-    if ((e = cudaOccupancyMaxActiveClusters(&n, batch_kernel, &cfg)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg)) != cudaSuccess) return e;
     if (n < 1) return cudaErrorInvalidConfiguration;
     bp->clusters = n;
     bp->dims = WsDims{(maxM + 3) / 4 * 4, maxN, maxK, C};
@@ -76,7 +80,7 @@ cudaError_t cached_plan(gspca_t h, int C, long maxM, int maxN, int maxK, BatchPl
         *bp = it->second;
         return cudaSuccess;
     }
-    const cudaError_t e = plan_batch(h->device, C, maxM, maxN, maxK, bp);
+    const cudaError_t e = plan_batch(h->device, h->dtype, C, maxM, maxN, maxK, bp);
     if (e == cudaSuccess) h->batch.plans[key] = *bp;
     return e;
 }
@@ -122,7 +126,6 @@ gspca_status check_batch(gspca_t h, const gspca_problem* p, int count, double to
         if (q.M > h->max_M || q.N > h->max_N || q.K > h->max_K) return GSPCA_ERR_INVALID_ARG;
         if (q.N > kBatchMaxN) return GSPCA_ERR_NOT_SUPPORTED;
     }
-    if (h->dtype != GSPCA_F32) return GSPCA_ERR_NOT_SUPPORTED;
     return GSPCA_OK;
 }
 
@@ -222,7 +225,7 @@ gspca_status enqueue_batch(gspca_t h, cudaStream_t s, const gspca_problem* p, in
             d.pad = 0;
         }
         void* args[] = {a.get()};
-        GS_CUDA(cudaLaunchKernelExC(&cfg, (const void*)batch_kernel, args));
+        GS_CUDA(cudaLaunchKernelExC(&cfg, batch_kernel_for(h->dtype), args));
         ++n;
     }
     if (events) GS_CUDA(cudaEventRecord(b.e1, s));

@@ -94,10 +94,12 @@ __device__ __forceinline__ T* shift(T* p, size_t bytes) {
 }
 
 // Pack this CTA's panels [p0, p1) of X (column-major, ldx) into the panel
-// layout R[(p*N + c)*4 + q] through a 16-column x 128-row shared tile
-// (rows past M are zero).  Returns this CTA's float-float sum of x^2.
-__device__ __forceinline__ ff pack_panels(const float* __restrict__ X, long long ldx, int M, int N, int p0, int p1,
-                                          float* __restrict__ R, SmemFit& sm) {
+// layout (row 4p+q, column c in element q of cell p*ldp + c, Cell<E> storage)
+// through a 16-column x 128-row shared tile (rows past M are zero).  Returns
+// this CTA's float-float sum of the stored values squared.
+template <class E>
+__device__ __forceinline__ ff pack_panels(const float* __restrict__ X, long long ldx, int M, int N, int ldp, int p0,
+                                          int p1, void* __restrict__ R, SmemFit& sm) {
     float* tile = &sm.tmpf[0][0];  // 16 x 128, rows XOR-swizzled by column
     const int t = threadIdx.x;
     ff acc = ff_zero();
@@ -110,7 +112,7 @@ __device__ __forceinline__ ff pack_panels(const float* __restrict__ X, long long
                 for (int i = 0; i < 4; ++i) {
                     const int c = cc + 4 * i, col = ct + c, row = 4 * pt + rr;
                     float v = 0.f;
-                    if (col < N && rr < rows && row < M) v = X[(size_t)col * ldx + row];
+                    if (col < N && rr < rows && row < M) v = Cell<E>::q1(X[(size_t)col * ldx + row]);
                     acc = ff_add(acc, ff_sqr(v));
                     tile[c * 128 + (rr ^ ((c & 7) << 2))] = v;
                 }
@@ -120,7 +122,7 @@ __device__ __forceinline__ ff pack_panels(const float* __restrict__ X, long long
             for (int i = 0; i < 4; ++i) {
                 const int e = t + 512 * i, pl = e >> 6, w = e & 63, c = w >> 2, q = w & 3;
                 if (4 * pl < rows && ct + c < N)
-                    R[((size_t)(pt + pl) * N + ct + c) * 4 + q] = tile[c * 128 + ((pl * 4 + q) ^ ((c & 7) << 2))];
+                    Cell<E>::st1(R, (size_t)(pt + pl) * ldp + ct + c, q, tile[c * 128 + ((pl * 4 + q) ^ ((c & 7) << 2))]);
             }
             __syncthreads();
         }
@@ -128,10 +130,10 @@ __device__ __forceinline__ ff pack_panels(const float* __restrict__ X, long long
     return acc;
 }
 
-template <int CPT>
-__device__ __forceinline__ void ring_geometry(int N, int ring_bytes, int* S, int* groups) {
+template <int CPT, class E>
+__device__ __forceinline__ void ring_geometry(int ldp, int ring_bytes, int* S, int* groups) {
     constexpr int PPR = PassShape<CPT>::PPR;
-    const int stage1 = N * 16;
+    const int stage1 = ldp * Cell<E>::kBytes;
     int s = min(kMaxStages, ring_bytes / stage1) & ~1;
     if (CPT >= 2 && CPT <= 4 && s >= 4) {
         *S = s;
@@ -143,26 +145,28 @@ __device__ __forceinline__ void ring_geometry(int N, int ring_bytes, int* S, int
     *groups = 1;
 }
 
-template <int CPT>
+template <int CPT, class E>
 __device__ __forceinline__ FitOutcome run_problem(FitArgs& fa, const TeamCluster& tm, SmemFit& sm,
                                                   unsigned char* dyn_smem, Ring& rg, float threshf, unsigned& epoch,
                                                   bool narrow) {
     int S = 0, groups = 1;
-    if (!narrow) ring_geometry<CPT>(fa.N, fa.ring_bytes, &S, &groups);
+    if (!narrow) ring_geometry<CPT, E>(fa.ldp, fa.ring_bytes, &S, &groups);
     if (threadIdx.x == 0) {
         fa.tma_stages = S;
         fa.dot_groups = groups;
         fa.narrow = narrow ? 1 : 0;
     }
     __syncthreads();
-    ring_setup(rg, sm, dyn_smem, S, groups == 2 ? 1 : PassShape<CPT>::PPR, fa.N);
-    const FitOutcome r = fit_one<CPT>(fa, tm, sm, dyn_smem, rg, threshf, epoch);
+    ring_setup(rg, sm, dyn_smem, S, groups == 2 ? 1 : PassShape<CPT>::PPR, fa.ldp * Cell<E>::kBytes);
+    const FitOutcome r = fit_one<CPT, E>(fa, tm, sm, dyn_smem, rg, threshf, epoch);
     ring_drain(fa, rg);
     return r;
 }
 
 // One launch: clusters of C CTAs take problems from ctl->queue until it runs
-// past count.  Columns per thread are 1 (N <= 512) or 2 (N <= 1024).
+// past count.  Columns per thread are 1 (N <= 512) or 2 (N <= 1024).  E is the
+// storage type of R (float or __nv_bfloat16).
+template <class E>
 __global__ void __launch_bounds__(kBlock, 1) batch_kernel(const __grid_constant__ BatchArgs a) {
     __shared__ SmemFit sm;
     __shared__ FitArgs fa;
@@ -224,6 +228,7 @@ __global__ void __launch_bounds__(kBlock, 1) batch_kernel(const __grid_constant_
             f.tol = a.tol;
             f.eps_thresh = a.eps_thresh;
             f.R = shift(a.ws.R, off);
+            f.ldp = panel_cells(N, Cell<E>::kBytes);
             f.V = shift(a.ws.V, off);
             f.ldv = a.ws.ld;
             f.U = shift(a.ws.U, off);
@@ -253,7 +258,7 @@ __global__ void __launch_bounds__(kBlock, 1) batch_kernel(const __grid_constant_
         }
         __syncthreads();
         // pack, ||X||_F^2 over the team
-        ff ss = pack_panels(pb.X, pb.ldx, M, N, p0, p1, fa.R, sm);
+        ff ss = pack_panels<E>(pb.X, pb.ldx, M, N, fa.ldp, p0, p1, fa.R, sm);
         fence_proxy_async_global();  // the ring reads R through the async proxy
         ss = block_sum_ff(ss, sm);
         write_scalar(fa, rank, 0, ss);
@@ -262,8 +267,8 @@ __global__ void __launch_bounds__(kBlock, 1) batch_kernel(const __grid_constant_
         const float threshf =
             (float)(fa.eps_thresh * sqrt(fmax(0.0, ff_to_double(sm.sff[0]))));
         const bool narrow = a.pass == 1;
-        FitOutcome r = (N <= kBlock) ? run_problem<1>(fa, tm, sm, dyn_smem, rg, threshf, epoch, narrow)
-                                     : run_problem<2>(fa, tm, sm, dyn_smem, rg, threshf, epoch, narrow);
+        FitOutcome r = (N <= kBlock) ? run_problem<1, E>(fa, tm, sm, dyn_smem, rg, threshf, epoch, narrow)
+                                     : run_problem<2, E>(fa, tm, sm, dyn_smem, rg, threshf, epoch, narrow);
         PHASE_MARK(15);
         tm.sync(epoch, nullptr);  // V, U, lambda of every CTA visible; failure word settled
         if (ldcg(fail_word) != 0) {
@@ -302,7 +307,7 @@ __global__ void __launch_bounds__(kBlock, 1) batch_kernel(const __grid_constant_
         if (rank == 0 && tid == 0) {
             double bytes = 0.0;
             long long tot = 0;
-            const double mn = (double)M * N * 4.0;
+            const double mn = (double)M * N * (Cell<E>::kBytes / 4);
             for (int k = 0; k < K; ++k) {
                 const int it = k < found ? ldcg(fa.iters + k) : 0;
                 pb.lambda[k] = k < found ? ldcg(fa.lam + k) : 0.0;
@@ -324,5 +329,10 @@ __global__ void __launch_bounds__(kBlock, 1) batch_kernel(const __grid_constant_
         for (int s = 0; s < sm.mbar_live; ++s)
             asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(&sm.mbar[s])) : "memory");
 }
+
+// The batched kernel of a storage type as a launchable function pointer
+// (defined and instantiated with the kernels, see fit_inst.cuh).
+template <class E>
+const void* batch_kernel_ptr();
 
 }  // namespace gspca

@@ -2,6 +2,7 @@
 // warp reductions, the bounded grid barrier and the TMA bulk-copy ring.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -291,5 +292,93 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
 }
 
 __device__ __forceinline__ float4 lds128(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+// ---------------------------------------------------------------- storage of R
+
+// R is stored in 4-row panels; a cell is the 4 rows of one panel in one column,
+// and cell i of the panel array sits at byte offset i * Cell<E>::kBytes.
+//   Cell<float>         : 16 bytes, four FP32 values.
+//   Cell<__nv_bfloat16> : 8 bytes, four bfloat16 values; a value is rounded to
+//                         the nearest bfloat16 (ties to even) when it is stored,
+//                         and widened exactly to FP32 when it is loaded.
+// quant(v) is the value a store followed by a load gives back, so a pass that
+// writes R (the fused deflation) goes on with exactly what later passes read.
+// A panel holds ldp cells (panel_cells): N, or N rounded up to even for
+// bfloat16 so that every panel starts on a 16-byte boundary (TMA bulk copies).
+template <class E>
+struct Cell;
+
+template <>
+struct Cell<float> {
+    static constexpr int kBytes = 16;
+    static __device__ __forceinline__ float4 ldg(const void* R, size_t i) {
+        return ld_stream4(static_cast<const float*>(R) + i * 4);
+    }
+    static __device__ __forceinline__ float4 ldg_plain(const void* R, size_t i) {
+        return reinterpret_cast<const float4*>(R)[i];
+    }
+    static __device__ __forceinline__ void stg(void* R, size_t i, float4 v) { st_stream4(static_cast<float*>(R) + i * 4, v); }
+    static __device__ __forceinline__ void stg_plain(void* R, size_t i, float4 v) { reinterpret_cast<float4*>(R)[i] = v; }
+    static __device__ __forceinline__ void st1(void* R, size_t i, int q, float v) { static_cast<float*>(R)[i * 4 + q] = v; }
+    static __device__ __forceinline__ float4 lds(const void* s, size_t i) {
+        return *reinterpret_cast<const float4*>(static_cast<const unsigned char*>(s) + i * 16);
+    }
+    static __device__ __forceinline__ float q1(float v) { return v; }
+    static __device__ __forceinline__ float4 quant(float4 v) { return v; }
+    static __device__ __forceinline__ void cp_async(void* dst, const void* src) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+    }
+};
+
+// Two bfloat16 in one 32-bit word: element 0 in the low half (lower address).
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+__device__ __forceinline__ uint32_t bf_pack(float lo, float hi) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&b);
+}
+__device__ __forceinline__ float4 bf_unpack(uint2 w) {
+    return make_float4(bf_lo(w.x), bf_hi(w.x), bf_lo(w.y), bf_hi(w.y));
+}
+
+template <>
+struct Cell<__nv_bfloat16> {
+    static constexpr int kBytes = 8;
+    static __device__ __forceinline__ float4 ldg(const void* R, size_t i) {
+        uint2 w;
+        asm volatile("ld.global.cg.v2.u32 {%0,%1}, [%2];"
+                     : "=r"(w.x), "=r"(w.y)
+                     : "l"(static_cast<const unsigned char*>(R) + i * 8));
+        return bf_unpack(w);
+    }
+    static __device__ __forceinline__ float4 ldg_plain(const void* R, size_t i) {
+        return bf_unpack(reinterpret_cast<const uint2*>(R)[i]);
+    }
+    static __device__ __forceinline__ uint2 pack(float4 v) { return make_uint2(bf_pack(v.x, v.y), bf_pack(v.z, v.w)); }
+    static __device__ __forceinline__ void stg(void* R, size_t i, float4 v) {
+        const uint2 w = pack(v);
+        asm volatile("st.global.cg.v2.u32 [%0], {%1,%2};" ::"l"(static_cast<unsigned char*>(R) + i * 8), "r"(w.x),
+                     "r"(w.y)
+                     : "memory");
+    }
+    static __device__ __forceinline__ void stg_plain(void* R, size_t i, float4 v) {
+        reinterpret_cast<uint2*>(R)[i] = pack(v);
+    }
+    static __device__ __forceinline__ void st1(void* R, size_t i, int q, float v) {
+        static_cast<__nv_bfloat16*>(R)[i * 4 + q] = __float2bfloat16_rn(v);
+    }
+    static __device__ __forceinline__ float4 lds(const void* s, size_t i) {
+        return bf_unpack(*reinterpret_cast<const uint2*>(static_cast<const unsigned char*>(s) + i * 8));
+    }
+    static __device__ __forceinline__ float q1(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+    static __device__ __forceinline__ float4 quant(float4 v) { return bf_unpack(pack(v)); }
+    static __device__ __forceinline__ void cp_async(void* dst, const void* src) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+    }
+};
+
+__host__ __device__ __forceinline__ int panel_cells(int N, int cell_bytes) {
+    return cell_bytes == 16 ? N : (N + 1) & ~1;
+}
 
 }  // namespace gspca

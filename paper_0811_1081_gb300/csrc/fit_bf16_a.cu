@@ -1,0 +1,7 @@
+// Kernels for storage type __nv_bfloat16: the fit kernel for 512 and 1024 columns per
+// CTA, the pack/unpack kernels and the batched kernel.
+#include "fit_inst.cuh"
+
+GSPCA_INSTANTIATE_FIT(1, __nv_bfloat16)
+GSPCA_INSTANTIATE_FIT(2, __nv_bfloat16)
+GSPCA_INSTANTIATE_AUX(__nv_bfloat16)

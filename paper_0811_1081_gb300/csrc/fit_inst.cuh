@@ -1,0 +1,66 @@
+// Definitions of the per-(columns per thread, storage type) kernel attribute
+// queries and launches declared in launch_common.cuh.  Included only by the
+// fit_*.cu translation units, each of which instantiates a few of them, so the
+// heavy kernels compile in parallel and once each.
+#pragma once
+
+// (launch_common.cuh is deliberately not included: its inline dispatchers name
+// every instantiation, which would compile them all in each unit.)
+#include "batch_kernel.cuh"
+#include "fit_kernel.cuh"
+#include "prep_kernels.cuh"
+
+namespace gspca {
+
+template <int CPT, class E>
+cudaError_t fit_attrs(size_t dyn, int* bps, int* static_smem) {
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, fit_kernel<CPT, E>);
+    if (e != cudaSuccess) return e;
+    *static_smem = (int)fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(fit_kernel<CPT, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fit_kernel<CPT, E>, kBlock, dyn);
+}
+
+template <int CPT, class E>
+cudaError_t launch_fit_t(const FitArgs& a, int G, size_t dyn, cudaStream_t s) {
+    void* args[] = {const_cast<FitArgs*>(&a)};
+    return cudaLaunchCooperativeKernel((const void*)fit_kernel<CPT, E>, dim3(G), dim3(kBlock), args, dyn, s);
+}
+
+template <class E>
+void launch_pack(dim3 grid, cudaStream_t s, const float* X, int layout, long ldx, int M, int N, int np, int ldp,
+                 int center, const double* cmean, const double* rmean, void* R, double* xpart, unsigned* flags,
+                 int nflags, int* abort, int* info, int ninfo) {
+    pack_kernel<E><<<grid, kPackThreads, 0, s>>>(X, layout, ldx, M, N, np, ldp, center, cmean, rmean, R, xpart,
+                                                 flags, nflags, abort, info, ninfo);
+}
+
+template <class E>
+void launch_unpack(dim3 grid, cudaStream_t s, const void* R, int M, int N, int np, int ldp, const float* V, int ldv,
+                   const float* U, int ldu, const double* lam, const int* info, int K, int gs, float* R_out) {
+    unpack_kernel<E><<<grid, kPackThreads, 0, s>>>(R, M, N, np, ldp, V, ldv, U, ldu, lam, info, K, gs, R_out);
+}
+
+template <class E>
+const void* batch_kernel_ptr() {
+    return (const void*)batch_kernel<E>;
+}
+
+}  // namespace gspca
+
+// Explicit instantiation of the kernels of one column-block count / storage type.
+#define GSPCA_INSTANTIATE_FIT(CPT, E)                                                                   \
+    template cudaError_t gspca::fit_attrs<CPT, E>(size_t, int*, int*);                                 \
+    template cudaError_t gspca::launch_fit_t<CPT, E>(const gspca::FitArgs&, int, size_t, cudaStream_t);
+
+// Explicit instantiation of the pack/unpack kernels and the batched kernel of a storage type.
+#define GSPCA_INSTANTIATE_AUX(E)                                                                            \
+    template void gspca::launch_pack<E>(dim3, cudaStream_t, const float*, int, long, int, int, int, int, int, \
+                                        const double*, const double*, void*, double*, unsigned*, int, int*,   \
+                                        int*, int);                                                           \
+    template void gspca::launch_unpack<E>(dim3, cudaStream_t, const void*, int, int, int, int, const float*,  \
+                                          int, const float*, int, const double*, const int*, int, int,        \
+                                          float*);                                                            \
+    template const void* gspca::batch_kernel_ptr<E>();

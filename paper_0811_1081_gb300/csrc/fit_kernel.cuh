@@ -52,7 +52,8 @@ struct FitArgs {
     double eps_thresh;        // degenerate threshold factor: lambda <= eps_thresh * ||X||_F
     const double* xpart;      // partial sums of squares of the packed X
     int nxpart;
-    float* R;                 // [np][N][4] panel layout (row 4p+q, column c) at ((p*N + c)*4 + q)
+    void* R;                  // [np][ldp] cells (Cell<E>): row 4p+q, column c in cell p*ldp + c
+    int ldp;                  // cells per panel (panel_cells(N, Cell<E>::kBytes))
     float* V;                 // Mp x ldv row-major: V[r*ldv + k]
     int ldv;
     float* U;                 // N x ldu row-major
@@ -144,32 +145,36 @@ struct PassShape {
 // stage q % S and completes phase (q / S) & 1 of that stage's mbarrier.  Only
 // thread 0 issues copies; every thread keeps the counters identically.
 struct Ring {
-    float* base;
+    unsigned char* base;
     unsigned long long* mbar;
     int S;
-    int stage_floats;
+    int stage_bytes;
     unsigned issued;  // sequences issued so far
     unsigned used;    // sequences consumed so far
 
-    __device__ __forceinline__ float* stage(unsigned q) const { return base + (size_t)(q % S) * stage_floats; }
+    __device__ __forceinline__ unsigned char* stage(unsigned q) const { return base + (size_t)(q % S) * stage_bytes; }
     __device__ __forceinline__ uint64_t* bar(unsigned q) const { return reinterpret_cast<uint64_t*>(&mbar[q % S]); }
 };
 
 // Issue round i (sequence rg.issued) of a pass over panels [p0, p1).
+template <class E>
 __device__ __forceinline__ void ring_issue(const FitArgs& f, Ring& rg, int p0, int p1, int ppr, int i) {
+    constexpr int CB = Cell<E>::kBytes;
     const unsigned q = rg.issued;
     const int pa = p0 + i * ppr;
     const int npan = min(ppr, p1 - pa);
     if (threadIdx.x == 0)
-        tma_load_1d(rg.stage(q), f.R + (size_t)pa * f.N * 4, (uint32_t)npan * (uint32_t)f.N * 16u, rg.bar(q));
+        tma_load_1d(rg.stage(q), static_cast<const unsigned char*>(f.R) + (size_t)pa * f.ldp * CB,
+                    (uint32_t)npan * (uint32_t)f.ldp * (uint32_t)CB, rg.bar(q));
     rg.issued = q + 1;
 }
 
 // Issue the first rounds of the next pass (e.g. before the barrier preceding it).
+template <class E>
 __device__ __forceinline__ void ring_prefetch(const FitArgs& f, Ring& rg, int p0, int p1, int ppr) {
     if (rg.S == 0) return;
     const int nrounds = (p1 - p0 + ppr - 1) / ppr;
-    for (int i = (int)(rg.issued - rg.used); i < rg.S && i < nrounds; ++i) ring_issue(f, rg, p0, p1, ppr, i);
+    for (int i = (int)(rg.issued - rg.used); i < rg.S && i < nrounds; ++i) ring_issue<E>(f, rg, p0, p1, ppr, i);
 }
 
 // A ring wait that gave up after the caller's limit is reported as a timeout,
@@ -210,7 +215,7 @@ enum : int { kPassDot = 0, kPassCol = 1, kPassSq = 2 };
 //             sc = ||R(:, kcol)||^2 over the CTA's rows.  Register path.
 //   kPassSq : sacc = column sums of squares (start-column fallback).
 // Returns false (in every thread) if a bounded wait on the ring timed out.
-template <int CPT, int MODE>
+template <int CPT, int MODE, class E>
 __device__ __forceinline__ bool row_pass(const FitArgs& f, SmemFit& sm, Ring& rg, int p0, int p1,
                                          const float (&uc)[CPT], int kcol, bool deflate, float lamf, int kprev,
                                          float (&sacc)[CPT], ff& sc) {
@@ -219,6 +224,7 @@ __device__ __forceinline__ bool row_pass(const FitArgs& f, SmemFit& sm, Ring& rg
     constexpr int SH = 5 - Log2<RPR>::value;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int T = blockDim.x, N = f.N;
+    const size_t ldp = (size_t)f.ldp;
     const bool tma = (MODE == kPassDot) && rg.S > 0;
     int owner = -1;
     if (MODE == kPassCol && (kcol % T) == tid) owner = kcol / T;
@@ -226,7 +232,7 @@ __device__ __forceinline__ bool row_pass(const FitArgs& f, SmemFit& sm, Ring& rg
     for (int i = 0; i < CPT; ++i) sacc[i] = 0.f;
     ff my = ff_zero();
     int ok = 1;
-    if (tma) ring_prefetch(f, rg, p0, p1, PPR);
+    if (tma) ring_prefetch<E>(f, rg, p0, p1, PPR);
     const unsigned base = rg.used;
     int buf = 0;
     int round = 0;
@@ -239,13 +245,13 @@ __device__ __forceinline__ bool row_pass(const FitArgs& f, SmemFit& sm, Ring& rg
                 ok = 0;  // reported; the stage is still awaited before it is read or refilled
                 mbar_wait(rg.bar(q), (q / rg.S) & 1u, kSettleNs);
             }
-            const float* st = rg.stage(q);
+            const unsigned char* st = rg.stage(q);
 #pragma unroll
             for (int pp = 0; pp < PPR; ++pp) {
 #pragma unroll
                 for (int i = 0; i < CPT; ++i) {
                     const int c = tid + i * T;
-                    d[pp][i] = (pb + pp < p1 && c < N) ? lds128(st + ((size_t)pp * N + c) * 4)
+                    d[pp][i] = (pb + pp < p1 && c < N) ? Cell<E>::lds(st, (size_t)pp * ldp + c)
                                                        : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
@@ -256,7 +262,7 @@ __device__ __forceinline__ bool row_pass(const FitArgs& f, SmemFit& sm, Ring& rg
 #pragma unroll
                 for (int i = 0; i < CPT; ++i) {
                     const int c = tid + i * T;
-                    d[pp][i] = (p < p1 && c < N) ? ld_stream4(f.R + ((size_t)p * N + c) * 4)
+                    d[pp][i] = (p < p1 && c < N) ? Cell<E>::ldg(f.R, (size_t)p * ldp + c)
                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
@@ -279,8 +285,9 @@ __device__ __forceinline__ bool row_pass(const FitArgs& f, SmemFit& sm, Ring& rg
                     v.y = fmaf(-cf[1], uc[i], v.y);
                     v.z = fmaf(-cf[2], uc[i], v.z);
                     v.w = fmaf(-cf[3], uc[i], v.w);
+                    v = Cell<E>::quant(v);  // the stored residual, as later passes read it
                     d[pp][i] = v;
-                    if (p < p1 && c < N) st_stream4(f.R + ((size_t)p * N + c) * 4, v);
+                    if (p < p1 && c < N) Cell<E>::stg(f.R, (size_t)p * ldp + c, v);
                 }
             }
         }
@@ -307,7 +314,7 @@ __device__ __forceinline__ bool row_pass(const FitArgs& f, SmemFit& sm, Ring& rg
             // every thread has its panel data in registers: refill this stage
             if (tma) {
                 const int ahead = round + rg.S;
-                if (pb + rg.S * PPR < p1 && (int)(rg.issued - base) == ahead) ring_issue(f, rg, p0, p1, PPR, ahead);
+                if (pb + rg.S * PPR < p1 && (int)(rg.issued - base) == ahead) ring_issue<E>(f, rg, p0, p1, PPR, ahead);
             }
             float rs = 0.f;
             if (lane < RPR)
@@ -395,17 +402,18 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
 // r + S belongs to the same group as round r and that group refills its own
 // stages.  On return group 0 holds the CTA's s' partials and sc = sum v'^2.
 // Returns false (in every thread) if a bounded wait on the ring timed out.
-template <int CPT>
+template <int CPT, class E>
 __device__ __forceinline__ bool pass_dot2(const FitArgs& f, SmemFit& sm, Ring& rg, int p0, int p1,
                                           const float (&uc2)[2 * CPT], float (&sacc2)[2 * CPT], ff& sc) {
     constexpr int C2 = 2 * CPT;
     const int tid = threadIdx.x, grp = tid >> 8, lt = tid & 255, lane = tid & 31, lw = (tid >> 5) & 7;
-    const int N = f.N;
+    constexpr int CB = Cell<E>::kBytes;
+    const int N = f.N, ldp = f.ldp;
 #pragma unroll
     for (int i = 0; i < C2; ++i) sacc2[i] = 0.f;
     ff my = ff_zero();
     int ok = 1;
-    ring_prefetch(f, rg, p0, p1, 1);
+    ring_prefetch<E>(f, rg, p0, p1, 1);
     const unsigned base = rg.used;
     const int nrounds = p1 - p0;
     for (int round = grp; round < nrounds; round += 2) {
@@ -416,12 +424,12 @@ __device__ __forceinline__ bool pass_dot2(const FitArgs& f, SmemFit& sm, Ring& r
             ok = 0;  // reported; the stage is still awaited before it is read or refilled
             mbar_wait(rg.bar(q), (q / rg.S) & 1u, kSettleNs);
         }
-        const float* st = rg.stage(q);
+        const unsigned char* st = rg.stage(q);
         float4 d[C2];
 #pragma unroll
         for (int i = 0; i < C2; ++i) {
             const int c = lt + i * 256;
-            d[i] = c < N ? lds128(st + (size_t)c * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            d[i] = c < N ? Cell<E>::lds(st, (size_t)c) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -437,7 +445,8 @@ __device__ __forceinline__ bool pass_dot2(const FitArgs& f, SmemFit& sm, Ring& r
         named_barrier(1 + grp, 256);
         // this group has read the stage: refill it with round + S (same group)
         if (lt == 0 && round + rg.S < nrounds)
-            tma_load_1d(rg.stage(q + rg.S), f.R + (size_t)(p + rg.S) * N * 4, (uint32_t)N * 16u, rg.bar(q + rg.S));
+            tma_load_1d(rg.stage(q + rg.S), static_cast<const unsigned char*>(f.R) + (size_t)(p + rg.S) * ldp * CB,
+                        (uint32_t)ldp * (uint32_t)CB, rg.bar(q + rg.S));
         float rs = 0.f;
         if (lane < 4)
 #pragma unroll
@@ -465,7 +474,7 @@ __device__ __forceinline__ bool pass_dot2(const FitArgs& f, SmemFit& sm, Ring& r
     }
     // group 1 hands its s' partials to group 0 through the (now idle) ring memory
     const int all_ok = __syncthreads_and(ok);
-    float* xch = rg.base;
+    float* xch = reinterpret_cast<float*>(rg.base);
     if (grp == 1)
 #pragma unroll
         for (int i = 0; i < C2; ++i) {
@@ -520,20 +529,19 @@ struct LdsTraits {
     static_assert(PP * CW * 16 == kLdsStageBytes, "one stage holds a round");
 };
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-template <int NJW, int TW>
+template <int NJW, int TW, class E>
 __device__ __forceinline__ bool pass_lds(const FitArgs& f, SmemFit& sm, int p0, int p1, const float* __restrict__ u_in,
                                          float* pA, ff& sc, unsigned char* dyn) {
     using B = LdsTraits<NJW, TW>;
     constexpr int PP = B::PP, CW = B::CW, NG = B::NG, GT = B::GT, V = B::V, SW = kLdsStages;
+    constexpr int CB = Cell<E>::kBytes;
+    const size_t ldp = (size_t)f.ldp;
     constexpr int SHIFT = 5 - Log2<V>::value;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int grp = warp / TW, wi = warp % TW;
@@ -557,8 +565,8 @@ __device__ __forceinline__ bool pass_lds(const FitArgs& f, SmemFit& sm, int p0, 
     const int nrounds = (npan + PP - 1) / PP;
     const int nr = nrounds > grp ? (nrounds - grp + NG - 1) / NG : 0;  // this group's rounds
     // piece (pp, j) of a round: panel pb + pp, column c0 + lane + 32 j, at
-    // stage offset (pp * NJW + j) * 512 + lane * 16 (a warp's copies of one
-    // piece index are 512 contiguous bytes on both sides)
+    // stage cell (pp * NJW + j) * 32 + lane (a warp's copies of one piece index
+    // are 32 contiguous cells on both sides)
     auto issue = [&](int i) {
         if (i < nr) {
             unsigned char* st = stages + (size_t)(i % SW) * kLdsStageBytes;
@@ -569,7 +577,9 @@ __device__ __forceinline__ bool pass_lds(const FitArgs& f, SmemFit& sm, int p0, 
                 for (int j = 0; j < NJW; ++j) {
                     const int c = lane + 32 * j;
                     if (pb + pp < p1 && c < cw)
-                        cp_async16(st + (pp * NJW + j) * 512 + lane * 16, f.R + ((size_t)(pb + pp) * N + c0 + c) * 4);
+                        Cell<E>::cp_async(st + ((pp * NJW + j) * 32 + lane) * CB,
+                                          static_cast<const unsigned char*>(f.R) +
+                                              ((size_t)(pb + pp) * ldp + c0 + c) * CB);
                 }
         }
         cp_async_commit();  // one group per round (possibly empty) keeps the counts uniform
@@ -579,14 +589,14 @@ __device__ __forceinline__ bool pass_lds(const FitArgs& f, SmemFit& sm, int p0, 
     for (int i = 0; i < nr; ++i) {
         const int pb = p0 + (grp + NG * i) * PP;
         cp_async_wait<SW - 1>();  // this lane's pieces of round i have landed
-        const unsigned char* sb = stages + (size_t)(i % SW) * kLdsStageBytes + lane * 16;
+        const unsigned char* sb = stages + (size_t)(i % SW) * kLdsStageBytes;
         float4 d[PP][NJW];
 #pragma unroll
         for (int pp = 0; pp < PP; ++pp)
 #pragma unroll
             for (int j = 0; j < NJW; ++j) {
                 const int c = lane + 32 * j;
-                d[pp][j] = (pb + pp < p1 && c < cw) ? *reinterpret_cast<const float4*>(sb + (pp * NJW + j) * 512)
+                d[pp][j] = (pb + pp < p1 && c < cw) ? Cell<E>::lds(sb, (size_t)((pp * NJW + j) * 32 + lane))
                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         float acc[V];
@@ -683,18 +693,18 @@ __device__ __forceinline__ bool pass_lds(const FitArgs& f, SmemFit& sm, int p0, 
 
 // pass_lds for the column count of f (N <= 512 when CPT == 1, N <= 1024 when
 // CPT == 2).
-template <int CPT>
+template <int CPT, class E>
 __device__ __forceinline__ bool pass_narrow(const FitArgs& f, SmemFit& sm, int p0, int p1, const float* u_in,
                                             float* pA, ff& sc, unsigned char* dyn) {
     const int nj = (f.N + 31) / 32;
     if constexpr (CPT == 1) {
-        if (nj <= 1) return pass_lds<1, 1>(f, sm, p0, p1, u_in, pA, sc, dyn);
-        if (nj <= 2) return pass_lds<2, 1>(f, sm, p0, p1, u_in, pA, sc, dyn);
-        if (nj <= 4) return pass_lds<4, 1>(f, sm, p0, p1, u_in, pA, sc, dyn);
-        if (nj <= 8) return pass_lds<8, 1>(f, sm, p0, p1, u_in, pA, sc, dyn);
-        return pass_lds<8, 2>(f, sm, p0, p1, u_in, pA, sc, dyn);
+        if (nj <= 1) return pass_lds<1, 1, E>(f, sm, p0, p1, u_in, pA, sc, dyn);
+        if (nj <= 2) return pass_lds<2, 1, E>(f, sm, p0, p1, u_in, pA, sc, dyn);
+        if (nj <= 4) return pass_lds<4, 1, E>(f, sm, p0, p1, u_in, pA, sc, dyn);
+        if (nj <= 8) return pass_lds<8, 1, E>(f, sm, p0, p1, u_in, pA, sc, dyn);
+        return pass_lds<8, 2, E>(f, sm, p0, p1, u_in, pA, sc, dyn);
     } else {
-        return pass_lds<8, 4>(f, sm, p0, p1, u_in, pA, sc, dyn);
+        return pass_lds<8, 4, E>(f, sm, p0, p1, u_in, pA, sc, dyn);
     }
 }
 
@@ -1043,9 +1053,10 @@ struct FitOutcome {
     bool alive;  // false: a bounded wait gave up, the kernel must leave
 };
 
-// (Re)initialise this CTA's ring for a problem with N columns: S stages of
-// ppr panels each.  Must be called with no copy in flight.
-__device__ __forceinline__ void ring_setup(Ring& rg, SmemFit& sm, unsigned char* dyn_smem, int S, int ppr, int N) {
+// (Re)initialise this CTA's ring: S stages of ppr panels of panel_bytes each.
+// Must be called with no copy in flight.
+__device__ __forceinline__ void ring_setup(Ring& rg, SmemFit& sm, unsigned char* dyn_smem, int S, int ppr,
+                                          int panel_bytes) {
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int s = 0; s < sm.mbar_live; ++s)
@@ -1056,8 +1067,8 @@ __device__ __forceinline__ void ring_setup(Ring& rg, SmemFit& sm, unsigned char*
     }
     __syncthreads();
     rg.S = S;
-    rg.stage_floats = ppr * N * 4;
-    rg.base = reinterpret_cast<float*>(dyn_smem);
+    rg.stage_bytes = ppr * panel_bytes;
+    rg.base = dyn_smem;
     rg.mbar = sm.mbar;
     rg.issued = rg.used = 0;
 }
@@ -1066,7 +1077,7 @@ __device__ __forceinline__ void ring_setup(Ring& rg, SmemFit& sm, unsigned char*
 // degenerate threshold and this CTA's shared memory; the ring must be set up
 // for f.N.  Writes V, U, W and lambda/iters for k < found; returns the
 // outcome (identical in every CTA of the team).
-template <int CPT, class Team>
+template <int CPT, class E, class Team>
 __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, unsigned char* dyn_smem, Ring& rg,
                               float threshf, unsigned& epoch) {
     constexpr int PPR = PassShape<CPT>::PPR;
@@ -1122,7 +1133,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
             const int c = tid + i * T;
             uc[i] = (defl && c < N) ? ldcg(f.ut + (size_t)buf * N + c) * inv_nu : 0.f;
         }
-        if (!row_pass<CPT, kPassCol>(f, sm, rg, p0, p1, uc, k, defl, lamf, k - 1, sacc, sc)) {
+        if (!row_pass<CPT, kPassCol, E>(f, sm, rg, p0, p1, uc, k, defl, lamf, k - 1, sacc, sc)) {
             if (tm.fail(f)) {
                 alive = false;
                 goto leave;
@@ -1147,7 +1158,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
         if (sm.sff[0].hi == 0.f && sm.sff[0].lo == 0.f) {
             // Zero start column: restart from the residual column of largest
             // norm (lowest index on ties); every column zero => rank exhausted.
-            if (!row_pass<CPT, kPassSq>(f, sm, rg, p0, p1, uc, 0, false, 0.f, 0, sacc, sc) && tm.fail(f)) {
+            if (!row_pass<CPT, kPassSq, E>(f, sm, rg, p0, p1, uc, 0, false, 0.f, 0, sacc, sc) && tm.fail(f)) {
                 alive = false;
                 goto leave;
             }
@@ -1187,7 +1198,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                 status = kStDegenerate;
                 break;
             }
-            if (!row_pass<CPT, kPassCol>(f, sm, rg, p0, p1, uc, kcol, false, 0.f, 0, sacc, sc)) {
+            if (!row_pass<CPT, kPassCol, E>(f, sm, rg, p0, p1, uc, kcol, false, 0.f, 0, sacc, sc)) {
                 if (tm.fail(f)) {
                     alive = false;
                     goto leave;
@@ -1260,7 +1271,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
         nq = block_sum_ff(nq, sm);
         write_scalar(f, g, 2 + nb, nq);
         buf = nb;
-        ring_prefetch(f, rg, p0, p1, ring_ppr);
+        ring_prefetch<E>(f, rg, p0, p1, ring_ppr);
         GS_SYNC();
 
         // ------------- power iterations
@@ -1272,7 +1283,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
             if constexpr (CPT <= 2) {
                 if (f.narrow) {
                     PHASE_MARK(2);
-                    pass_ok = pass_narrow<CPT>(f, sm, p0, p1, f.ut + (size_t)buf * N, pA, sc, dyn_smem);
+                    pass_ok = pass_narrow<CPT, E>(f, sm, p0, p1, f.ut + (size_t)buf * N, pA, sc, dyn_smem);
                     two_done = true;
                 }
             }
@@ -1285,7 +1296,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                         uc2[i] = (c < N) ? ldcg(f.ut + (size_t)buf * N + c) : 0.f;
                     }
                     PHASE_MARK(2);
-                    pass_ok = pass_dot2<CPT>(f, sm, rg, p0, p1, uc2, sacc2, sc);
+                    pass_ok = pass_dot2<CPT, E>(f, sm, rg, p0, p1, uc2, sacc2, sc);
                     if (tid < 256)
 #pragma unroll
                         for (int i = 0; i < 2 * CPT; ++i) {
@@ -1302,7 +1313,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                     uc[i] = (c < N) ? ldcg(f.ut + (size_t)buf * N + c) : 0.f;
                 }
                 PHASE_MARK(2);
-                pass_ok = row_pass<CPT, kPassDot>(f, sm, rg, p0, p1, uc, 0, false, 0.f, 0, sacc, sc);
+                pass_ok = row_pass<CPT, kPassDot, E>(f, sm, rg, p0, p1, uc, 0, false, 0.f, 0, sacc, sc);
 #pragma unroll
                 for (int i = 0; i < CPT; ++i) {
                     const int c = tid + i * T;
@@ -1447,7 +1458,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
             mu = lamff;
             write_scalar(f, g, 2 + nbuf, nq2);
             buf = nbuf;
-            ring_prefetch(f, rg, p0, p1, ring_ppr);
+            ring_prefetch<E>(f, rg, p0, p1, ring_ppr);
             PHASE_MARK(11);
             GS_SYNC();
         }
@@ -1461,7 +1472,7 @@ leave:
 // ------------------------------------------------------------------ kernels
 
 // Single problem, whole grid (cooperative launch).
-template <int CPT>
+template <int CPT, class E>
 __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
     __shared__ SmemFit sm;
     extern __shared__ __align__(128) unsigned char dyn_smem[];
@@ -1486,9 +1497,10 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
     __syncthreads();
     const float threshf = (float)(f.eps_thresh * sqrt(sm.dsc[0]));
     Ring rg;
-    ring_setup(rg, sm, dyn_smem, f.tma_stages, f.dot_groups == 2 ? 1 : PassShape<CPT>::PPR, f.N);
+    ring_setup(rg, sm, dyn_smem, f.tma_stages, f.dot_groups == 2 ? 1 : PassShape<CPT>::PPR,
+               f.ldp * Cell<E>::kBytes);
     unsigned epoch = 0;
-    const FitOutcome r = fit_one<CPT>(f, tm, sm, dyn_smem, rg, threshf, epoch);
+    const FitOutcome r = fit_one<CPT, E>(f, tm, sm, dyn_smem, rg, threshf, epoch);
 #ifdef GSPCA_PHASE_TIMING
     PHASE_MARK(15);
     if (blockIdx.x == 0 && tid == 0 && f.timing)

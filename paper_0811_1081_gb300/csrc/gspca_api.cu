@@ -55,7 +55,6 @@ gspca_status check_fit_args(gspca_t h, const void* X, gspca_layout layout, long 
             for (int k = 0; k < K; ++k)
                 if (opts->iters_lock[k] < 1) return GSPCA_ERR_INVALID_ARG;
     }
-    if (h->dtype != GSPCA_F32) return GSPCA_ERR_NOT_SUPPORTED;
     return GSPCA_OK;
 }
 
@@ -69,7 +68,7 @@ gspca_status enqueue_fit(gspca_t h, cudaStream_t s, const float* X, gspca_layout
     const int nxpart = ((N + 31) / 32) * ((np + 31) / 32);
     if (nxpart > h->ws.xcap) return GSPCA_ERR_NOT_SUPPORTED;
     Plan plan{};
-    GS_CUDA(plan_fit(h->device, h->num_sms, h->ws.G, M, N, K, opts, &plan));
+    GS_CUDA(plan_fit(h->device, h->num_sms, h->ws.G, M, N, K, cell_bytes(h->dtype), opts, &plan));
     const int* lock_dev = nullptr;
     if (opts && opts->iters_lock) {
         GS_CUDA(cudaMemcpyAsync(h->ws.lock, opts->iters_lock, sizeof(int) * K, cudaMemcpyHostToDevice, s));
@@ -94,11 +93,11 @@ gspca_status enqueue_fit(gspca_t h, cudaStream_t s, const float* X, gspca_layout
 }
 
 // Algorithmic bytes of the persistent kernel for a finished fit: per pass one
-// read of R (M x N FP32); per component one extra write of R (the fused
-// deflation); GS-PCA reads V_(k) twice (b', v') and U_(k) twice, W_(k) once
-// per iteration.
-double alg_bytes(int M, int N, int found, const int* iters, bool gs) {
-    const double mn = (double)M * N * 4.0;
+// read of R (M x N values of elem_bytes each); per component one extra write
+// of R (the fused deflation); GS-PCA reads the FP32 factors V_(k) twice (b',
+// v') and U_(k) twice, W_(k) once per iteration.
+double alg_bytes(int M, int N, int found, const int* iters, bool gs, double elem_bytes) {
+    const double mn = (double)M * N * elem_bytes;
     double b = 0.0;
     for (int k = 0; k < found; ++k) {
         const double passes = (double)iters[k] + 1.0;
@@ -130,7 +129,7 @@ gspca_status finish(gspca_t h, cudaStream_t s, int K, gspca_algo algo, int M, in
     const int st = h->h_info[kInfoStatus];
     h->last.found = h->h_info[kInfoFound];
     h->last.total_iters = (long long)h->h_info[kInfoItersLo] + ((long long)h->h_info[kInfoItersHi] << 31);
-    h->last.alg_bytes = alg_bytes(M, N, h->last.found, hiters, algo == GSPCA_GS);
+    h->last.alg_bytes = alg_bytes(M, N, h->last.found, hiters, algo == GSPCA_GS, cell_bytes(h->dtype) / 4.0);
     if (st == kStDegenerate) return GSPCA_ERR_DEGENERATE;
     if (st == kStNotConverged) return GSPCA_WARN_NOT_CONVERGED;
     return GSPCA_OK;

@@ -20,8 +20,12 @@ constexpr int kRedundantMax = 128;      // k up to which every CTA reduces a k-v
 
 struct Plan {
     int cpt, ppr, G, S, ldk, max_slice, groups;
+    int cb;  // bytes of one cell of R: 16 (FP32 storage) or 8 (bfloat16 storage)
     size_t dyn;
 };
+
+// Bytes of one cell of R (4 rows x 1 column) for a storage type.
+inline int cell_bytes(gspca_dtype dt) { return dt == GSPCA_BF16 ? 8 : 16; }
 
 inline int cpt_for(int N) {
     int c = 1;
@@ -29,31 +33,41 @@ inline int cpt_for(int N) {
     return c;
 }
 
-template <int CPT>
-inline cudaError_t fit_attrs(size_t dyn, int* bps, int* static_smem) {
-    cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, fit_kernel<CPT>);
-    if (e != cudaSuccess) return e;
-    *static_smem = (int)fa.sharedSizeBytes;
-    e = cudaFuncSetAttribute(fit_kernel<CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fit_kernel<CPT>, kBlock, dyn);
+// Kernel attributes and launches per (columns per thread, storage type).  They
+// are defined beside the kernels (fit_inst.cuh) and instantiated once each in
+// the fit_*.cu translation units, so the host-side units compile no kernel.
+template <int CPT, class E>
+cudaError_t fit_attrs(size_t dyn, int* bps, int* static_smem);
+template <int CPT, class E>
+cudaError_t launch_fit_t(const FitArgs& a, int G, size_t dyn, cudaStream_t s);
+template <class E>
+void launch_pack(dim3 grid, cudaStream_t s, const float* X, int layout, long ldx, int M, int N, int np, int ldp,
+                 int center, const double* cmean, const double* rmean, void* R, double* xpart, unsigned* flags,
+                 int nflags, int* abort, int* info, int ninfo);
+template <class E>
+void launch_unpack(dim3 grid, cudaStream_t s, const void* R, int M, int N, int np, int ldp, const float* V, int ldv,
+                   const float* U, int ldu, const double* lam, const int* info, int K, int gs, float* R_out);
+
+template <class E>
+inline cudaError_t fit_attrs_e(int cpt, size_t dyn, int* bps, int* st) {
+    switch (cpt) {
+        case 1: return fit_attrs<1, E>(dyn, bps, st);
+        case 2: return fit_attrs<2, E>(dyn, bps, st);
+        case 4: return fit_attrs<4, E>(dyn, bps, st);
+        case 8: return fit_attrs<8, E>(dyn, bps, st);
+        default: return fit_attrs<16, E>(dyn, bps, st);
+    }
 }
 
-inline cudaError_t fit_attrs_any(int cpt, size_t dyn, int* bps, int* st) {
-    switch (cpt) {
-        case 1: return fit_attrs<1>(dyn, bps, st);
-        case 2: return fit_attrs<2>(dyn, bps, st);
-        case 4: return fit_attrs<4>(dyn, bps, st);
-        case 8: return fit_attrs<8>(dyn, bps, st);
-        default: return fit_attrs<16>(dyn, bps, st);
-    }
+inline cudaError_t fit_attrs_any(int cpt, int cb, size_t dyn, int* bps, int* st) {
+    return cb == 8 ? fit_attrs_e<__nv_bfloat16>(cpt, dyn, bps, st) : fit_attrs_e<float>(cpt, dyn, bps, st);
 }
 
 // Grid size, ring depth and shared memory for one problem.  Gcap bounds the
 // grid (the partial buffers' row count).
-inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int K, const gspca_opts* opts,
+inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int K, int cb, const gspca_opts* opts,
                             Plan* p) {
+    p->cb = cb;
     p->cpt = cpt_for(N);
     p->ppr = p->cpt >= 8 ? 1 : 8 / p->cpt;
     const int np = (M + 3) / 4;
@@ -71,46 +85,46 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
     cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (e != cudaSuccess) return e;
     int bps = 0, st = 0;
-    e = fit_attrs_any(p->cpt, vec, &bps, &st);
+    e = fit_attrs_any(p->cpt, cb, vec, &bps, &st);
     if (e != cudaSuccess) return e;
     const long avail = (long)optin - st - (long)vec - 1024;
     // Preferred: the two-group loading pass with one panel per ring stage and an
     // even stage count; otherwise one group with PPR panels per stage.
     p->groups = 1;
-    size_t stage = (size_t)N * 16;
+    const size_t panel = (size_t)panel_cells(N, cb) * cb;
+    size_t stage = panel;
     int S = avail > 0 ? (int)(avail / (long)stage) : 0;
     if (S > kMaxStages) S = kMaxStages;
     S &= ~1;
     if (p->cpt >= 2 && p->cpt <= 4 && S >= 4) {
         p->groups = 2;
     } else {
-        stage = (size_t)p->ppr * N * 16;
+        stage = (size_t)p->ppr * panel;
         S = avail > 0 ? (int)(avail / (long)stage) : 0;
         if (S > kMaxStages) S = kMaxStages;
         if (S < 2) S = 0;
     }
     p->S = S;
     p->dyn = vec + (size_t)S * stage;
-    e = fit_attrs_any(p->cpt, p->dyn, &bps, &st);
+    e = fit_attrs_any(p->cpt, cb, p->dyn, &bps, &st);
     if (e != cudaSuccess) return e;
     if (bps < 1) return cudaErrorInvalidConfiguration;
     return cudaSuccess;
 }
 
-template <int CPT>
-inline cudaError_t launch_fit_t(const FitArgs& a, const Plan& p, cudaStream_t s) {
-    void* args[] = {const_cast<FitArgs*>(&a)};
-    return cudaLaunchCooperativeKernel((const void*)fit_kernel<CPT>, dim3(p.G), dim3(kBlock), args, p.dyn, s);
+template <class E>
+inline cudaError_t launch_fit_e(const FitArgs& a, const Plan& p, cudaStream_t s) {
+    switch (p.cpt) {
+        case 1: return launch_fit_t<1, E>(a, p.G, p.dyn, s);
+        case 2: return launch_fit_t<2, E>(a, p.G, p.dyn, s);
+        case 4: return launch_fit_t<4, E>(a, p.G, p.dyn, s);
+        case 8: return launch_fit_t<8, E>(a, p.G, p.dyn, s);
+        default: return launch_fit_t<16, E>(a, p.G, p.dyn, s);
+    }
 }
 
 inline cudaError_t launch_fit(const FitArgs& a, const Plan& p, cudaStream_t s) {
-    switch (p.cpt) {
-        case 1: return launch_fit_t<1>(a, p, s);
-        case 2: return launch_fit_t<2>(a, p, s);
-        case 4: return launch_fit_t<4>(a, p, s);
-        case 8: return launch_fit_t<8>(a, p, s);
-        default: return launch_fit_t<16>(a, p, s);
-    }
+    return p.cb == 8 ? launch_fit_e<__nv_bfloat16>(a, p, s) : launch_fit_e<float>(a, p, s);
 }
 
 // FitArgs for a problem on a carved workspace.
@@ -128,6 +142,7 @@ inline FitArgs make_args(const Workspace& w, const Plan& p, int M, int N, int K,
     a.xpart = w.xpart;
     a.nxpart = nxpart;
     a.R = w.R;
+    a.ldp = panel_cells(N, p.cb);
     a.V = w.V;
     a.ldv = w.ld;
     a.U = w.U;
@@ -177,8 +192,12 @@ inline cudaError_t enqueue_sequence(const Workspace& w, const Plan& p, FitArgs a
         ++n;
     }
     const dim3 pgrid((N + 31) / 32, (np + 31) / 32);
-    pack_kernel<<<pgrid, kPackThreads, 0, s>>>(X, (int)layout, ldx, M, N, np, center, w.cmean, w.rmean, w.R,
-                                               w.xpart, w.flags, 1, w.abort, w.info, kInfoWords);
+    if (p.cb == 8)
+        launch_pack<__nv_bfloat16>(pgrid, s, X, (int)layout, ldx, M, N, np, a.ldp, center, w.cmean, w.rmean, w.R,
+                                   w.xpart, w.flags, 1, w.abort, w.info, kInfoWords);
+    else
+        launch_pack<float>(pgrid, s, X, (int)layout, ldx, M, N, np, a.ldp, center, w.cmean, w.rmean, w.R, w.xpart,
+                           w.flags, 1, w.abort, w.info, kInfoWords);
     ++n;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -191,8 +210,12 @@ inline cudaError_t enqueue_sequence(const Workspace& w, const Plan& p, FitArgs a
                                           a.algo == GSPCA_GS, T, P, lambda, iters);
     ++n;
     if (R_out) {
-        unpack_kernel<<<pgrid, kPackThreads, 0, s>>>(w.R, M, N, np, w.V, w.ld, w.U, w.ld, w.lam, w.info, K,
-                                                     a.algo == GSPCA_GS, R_out);
+        if (p.cb == 8)
+            launch_unpack<__nv_bfloat16>(pgrid, s, w.R, M, N, np, a.ldp, w.V, w.ld, w.U, w.ld, w.lam, w.info, K,
+                                         a.algo == GSPCA_GS, R_out);
+        else
+            launch_unpack<float>(pgrid, s, w.R, M, N, np, a.ldp, w.V, w.ld, w.U, w.ld, w.lam, w.info, K,
+                                 a.algo == GSPCA_GS, R_out);
         ++n;
     }
     *launches = n;

@@ -35,16 +35,18 @@ static __global__ void rowmean_kernel(const float* X, int layout, long ldx, int 
     if (lane == 0) mean[r] = s / (double)N;
 }
 
-// Pack X (M x N, either layout) into R (4-row panels, padded rows zero), with
-// optional subtraction of column means (center 1) or row means (center 2).
-// Each block writes the FP64 sum of squares of its tile to xpart.  Block
+// Pack X (M x N, either layout) into R (4-row panels of ldp cells, padded rows
+// zero, Cell<E> storage), with optional subtraction of column means (center 1)
+// or row means (center 2).  Each block writes the FP64 sum of squares of its
+// tile (of the stored values) to xpart.  Block
 // (0,0) also clears the fit kernel's barrier words (one every 32), abort flag
 // and info words: everything the fit needs to start at zero.
 // Tile: 32 columns x 32 panels (128 rows); 256 threads.
-static __global__ void __launch_bounds__(kPackThreads) pack_kernel(const float* __restrict__ X, int layout, long ldx,
-                                                            int M, int N, int np, int center,
+template <class E>
+__global__ void __launch_bounds__(kPackThreads) pack_kernel(const float* __restrict__ X, int layout, long ldx,
+                                                            int M, int N, int np, int ldp, int center,
                                                             const double* __restrict__ cmean,
-                                                            const double* __restrict__ rmean, float* R,
+                                                            const double* __restrict__ rmean, void* R,
                                                             double* xpart, unsigned* flags, int nflags, int* abort,
                                                             int* info, int ninfo) {
     __shared__ float tile[32][129];
@@ -89,13 +91,13 @@ static __global__ void __launch_bounds__(kPackThreads) pack_kernel(const float* 
         for (int pp = t >> 5; pp < 32; pp += kPackThreads / 32) {
             const int p = p0 + pp, c = c0 + cc;
             if (p < np && c < N) {
-                float4 v = make_float4(tile[cc][pp * 4 + 0], tile[cc][pp * 4 + 1], tile[cc][pp * 4 + 2],
-                                       tile[cc][pp * 4 + 3]);
+                float4 v = Cell<E>::quant(make_float4(tile[cc][pp * 4 + 0], tile[cc][pp * 4 + 1],
+                                                      tile[cc][pp * 4 + 2], tile[cc][pp * 4 + 3]));
                 sq = fmaf(v.x, v.x, sq);
                 sq = fmaf(v.y, v.y, sq);
                 sq = fmaf(v.z, v.z, sq);
                 sq = fmaf(v.w, v.w, sq);
-                *reinterpret_cast<float4*>(R + ((size_t)p * N + c) * 4) = v;
+                Cell<E>::stg_plain(R, (size_t)p * ldp + c, v);
             }
         }
     }
@@ -153,8 +155,10 @@ static __global__ void epilogue_kernel(const float* __restrict__ V, int ldv, con
 
 // R_out (M x N, ld M) from the panels; when every component was found the
 // deflation of the last one, R <- R - mult * V(K-1) U(K-1)^T (Eq. 3), is
-// applied here (inside the fit it happens in the next component's first pass).
-static __global__ void __launch_bounds__(kPackThreads) unpack_kernel(const float* __restrict__ R, int M, int N, int np,
+// applied here (inside the fit it happens in the next component's first pass)
+// and rounded as the storage of R rounds it.
+template <class E>
+__global__ void __launch_bounds__(kPackThreads) unpack_kernel(const void* __restrict__ R, int M, int N, int np, int ldp,
                                                               const float* __restrict__ V, int ldv,
                                                               const float* __restrict__ U, int ldu,
                                                               const double* __restrict__ lam_ws,
@@ -174,7 +178,7 @@ static __global__ void __launch_bounds__(kPackThreads) unpack_kernel(const float
             const int p = p0 + pp;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (p < np && c < N) {
-                v = *reinterpret_cast<const float4*>(R + ((size_t)p * N + c) * 4);
+                v = Cell<E>::ldg_plain(R, (size_t)p * ldp + c);
                 if (defl) {
                     float cf[4];
                     for (int q = 0; q < 4; ++q) {
@@ -185,6 +189,7 @@ static __global__ void __launch_bounds__(kPackThreads) unpack_kernel(const float
                     v.y = fmaf(-cf[1], uk, v.y);
                     v.z = fmaf(-cf[2], uk, v.z);
                     v.w = fmaf(-cf[3], uk, v.w);
+                    v = Cell<E>::quant(v);
                 }
             }
             tile[cc][pp * 4 + 0] = v.x;
