@@ -19,6 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "warmstart.c")]
 _SO = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -30,9 +31,9 @@ STATUS = {0: "ok", 1: "invalid argument", 4: "not converged", 5: "degenerate"}
 
 def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so (gcc, -O2 as in the paper's Sec. 3 build line)."""
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-               _SRC, "-o", _SO + ".tmp", "-lm"]
+    if force or not os.path.exists(_SO) or any(os.path.getmtime(_SO) < os.path.getmtime(f) for f in _SRCS):
+        cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
+               *_SRCS, "-o", _SO + ".tmp", "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(_SO + ".tmp", _SO)
     return _SO
@@ -48,7 +49,17 @@ def _load():
             ip = ctypes.POINTER(ctypes.c_int)
             lib.oracle_fit.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int,
-                                       dp, dp, dp, ip, dp, ip]
+                                       dp, dp, ip, dp, dp, dp, dp, ip, dp, ip]
+            lib.oracle_ws_nparams.restype = ctypes.c_int
+            lib.oracle_ws_features.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp]
+            lib.oracle_ws_features.restype = ctypes.c_int
+            lib.oracle_ws_forward.argtypes = [dp, dp, ctypes.c_int, dp]
+            lib.oracle_ws_forward.restype = None
+            lib.oracle_ws_loss_grad.argtypes = [dp, dp, dp, ip, ctypes.c_int, dp]
+            lib.oracle_ws_loss_grad.restype = ctypes.c_double
+            lib.oracle_ws_adam.argtypes = [dp, dp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_int]
+            lib.oracle_ws_adam.restype = None
             lib.oracle_round_bf16.argtypes = [ctypes.c_double]
             lib.oracle_round_bf16.restype = ctypes.c_double
             lib.oracle_fit.restype = ctypes.c_int
@@ -80,17 +91,21 @@ class Fit:
     R: np.ndarray        # M×N final residual
     found: int           # components extracted
     status: int          # 0 ok, 4 not converged, 5 degenerate
+    ws_choice: np.ndarray | None = None  # per component: 1 if the learned start was used
+    ws_rho: np.ndarray | None = None     # per component: (rho_plain, rho_learned)
 
 
 STORAGE = {"f64": 0, "bf16": 1}
 
 
 def fit(X: np.ndarray, K: int, tol: float = 1e-6, max_iter: int = 1000, algo: int | str = GS,
-        center: int = CENTER_NONE, iters_lock=None, storage: str = "f64") -> Fit:
+        center: int = CENTER_NONE, iters_lock=None, storage: str = "f64", ws_net=None, ws_G=None) -> Fit:
     """Run NIPALS-PCA (algo=0/'nipals') or GS-PCA (algo=1/'gs') on X (M×N) in FP64.
 
     storage="bf16": the residual R is rounded to bfloat16 after centring and after
-    every deflation (Eq. 3); all arithmetic stays FP64."""
+    every deflation (Eq. 3); all arithmetic stays FP64.
+    ws_net (5377 parameters) and ws_G (M×16 sketch): GS-PCA with the learned warm start
+    (warmstart.c)."""
     if isinstance(algo, str):
         algo = {"nipals": NIPALS, "gs": GS}[algo.lower()]
     X = np.asfortranarray(np.asarray(X, dtype=np.float64))
@@ -106,12 +121,67 @@ def fit(X: np.ndarray, K: int, tol: float = 1e-6, max_iter: int = 1000, algo: in
         lock = np.ascontiguousarray(np.asarray(iters_lock, dtype=np.int32))
         if lock.shape != (K,):
             raise ValueError("iters_lock must have K entries")
+    net = G = choice = rho = None
+    if ws_net is not None:
+        net = np.ascontiguousarray(np.asarray(ws_net, dtype=np.float64))
+        G = np.ascontiguousarray(np.asarray(ws_G, dtype=np.float64)[:M])
+        if net.shape != (ws_nparams(),) or G.shape != (M, 16):
+            raise ValueError("ws_net must hold 5377 parameters and ws_G at least M x 16 values")
+        choice = np.zeros(K, dtype=np.int32)
+        rho = np.zeros(2 * K, dtype=np.float64)
+    nul = ctypes.POINTER(ctypes.c_double)()
     st = _load().oracle_fit(algo, _dptr(X), M, N, K, float(tol), int(max_iter), int(center),
-                            _iptr(lock), STORAGE[storage], _dptr(T), _dptr(P), _dptr(lam), _iptr(iters),
-                            _dptr(R), _iptr(found))
+                            _iptr(lock), STORAGE[storage], _dptr(net) if net is not None else nul,
+                            _dptr(G) if G is not None else nul, _iptr(choice), _dptr(rho) if rho is not None else nul,
+                            _dptr(T), _dptr(P), _dptr(lam), _iptr(iters), _dptr(R), _iptr(found))
     if st == 1:
         raise ValueError("oracle_fit: invalid argument")
-    return Fit(T=T, P=P, lam=lam, iters=iters, R=R, found=int(found[0]), status=int(st))
+    return Fit(T=T, P=P, lam=lam, iters=iters, R=R, found=int(found[0]), status=int(st), ws_choice=choice,
+               ws_rho=None if rho is None else rho.reshape(K, 2))
+
+
+# ------------------------------------------------------------ learned warm start
+
+def ws_nparams() -> int:
+    return int(_load().oracle_ws_nparams())
+
+
+def ws_features(R: np.ndarray, G: np.ndarray) -> np.ndarray:
+    """Features (N×17) of every column of the residual R (M×N) with sketch G (M×16)."""
+    R = np.asfortranarray(np.asarray(R, dtype=np.float64))
+    M, N = R.shape
+    G = np.ascontiguousarray(np.asarray(G, dtype=np.float64)[:M])
+    out = np.zeros((N, 17), dtype=np.float64)
+    if _load().oracle_ws_features(_dptr(R), M, N, _dptr(G), _dptr(out)) != 0:
+        raise ValueError("oracle_ws_features: invalid argument")
+    return out
+
+
+def ws_forward(net: np.ndarray, feat: np.ndarray) -> np.ndarray:
+    """Network output w (one value per feature row)."""
+    net = np.ascontiguousarray(np.asarray(net, dtype=np.float64))
+    feat = np.ascontiguousarray(np.asarray(feat, dtype=np.float64))
+    w = np.zeros(feat.shape[0], dtype=np.float64)
+    _load().oracle_ws_forward(_dptr(net), _dptr(feat), feat.shape[0], _dptr(w))
+    return w
+
+
+def ws_loss_grad(net, feat, target, offsets):
+    """(mean loss, gradient) over instances; instance i owns rows offsets[i]:offsets[i+1]."""
+    net = np.ascontiguousarray(np.asarray(net, dtype=np.float64))
+    feat = np.ascontiguousarray(np.asarray(feat, dtype=np.float64))
+    target = np.ascontiguousarray(np.asarray(target, dtype=np.float64))
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    g = np.zeros(ws_nparams(), dtype=np.float64)
+    loss = _load().oracle_ws_loss_grad(_dptr(net), _dptr(feat), _dptr(target), _iptr(offs), len(offs) - 1,
+                                       _dptr(g))
+    return float(loss), g
+
+
+def ws_adam(net, m, v, grad, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step in place on float64 arrays net, m, v."""
+    _load().oracle_ws_adam(_dptr(net), _dptr(m), _dptr(v), _dptr(np.ascontiguousarray(grad, dtype=np.float64)),
+                           int(t), float(lr), float(b1), float(b2), float(eps), len(net))
 
 
 def round_bf16(x) -> np.ndarray:

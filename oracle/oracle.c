@@ -47,6 +47,10 @@
 #define OR_NOT_CONVERGED 4
 #define OR_DEGENERATE 5
 
+/* Learned warm start (warmstart.c). */
+int oracle_ws_choose_start(const double *R, int M, int N, int col, const double *G, const double *net, double *v,
+                           double *rho);
+
 /* ---------------------------------------------------------------- helpers */
 
 /* Largest finite bfloat16: (2 - 2^-7) * 2^127. */
@@ -314,6 +318,7 @@ static int nipals(double *R, int M, int N, int K, double tol, int max_iter,
  * norm); the scaling T = V Lambda happens once at the end. */
 static int gspca(double *R, int M, int N, int K, double tol, int max_iter,
                  const int *iters_lock, double thresh, int storage,
+                 const double *ws_net, const double *ws_G, int *ws_choice, double *ws_rho,
                  double *T, double *P, double *lambda, int *iters, int *found)
 {
     int not_converged = 0, status = OR_OK, kfound = K;
@@ -330,6 +335,14 @@ static int gspca(double *R, int M, int N, int K, double tol, int max_iter,
             break;
         }
         memcpy(v, R + (size_t)c * M, sizeof(double) * M);
+        if (ws_net) {
+            /* learned candidate, considered only when the paper's start column is nonzero */
+            int use = 0;
+            if (c == k)
+                use = oracle_ws_choose_start(R, M, N, c, ws_G, ws_net, v, ws_rho ? ws_rho + 2 * k : NULL);
+            if (ws_choice)
+                ws_choice[k] = use;
+        }
         double mu = 0.0, lam = 0.0;
         int j = 0, degenerate = 0;
         for (;;) {
@@ -384,10 +397,15 @@ static int gspca(double *R, int M, int N, int K, double tol, int max_iter,
  * iters_lock (nullable): run exactly iters_lock[k] iterations for component k
  * and ignore the convergence test (used to replay another implementation's
  * iteration counts).  storage: 0 = R kept in FP64; 1 = R rounded to bfloat16
- * after centring and after every deflation.  Outputs: T (M x K), P (N x K),
- * lambda (K), iters (K), found (number of components extracted). */
+ * after centring and after every deflation.  ws_net / ws_G (nullable, GS-PCA
+ * only): parameters and sketch of the learned warm start (warmstart.c);
+ * ws_choice (K ints) and ws_rho (2K doubles) receive, per component, whether
+ * the learned start was used and the two Rayleigh quotients compared.
+ * Outputs: T (M x K), P (N x K), lambda (K), iters (K), found (number of
+ * components extracted). */
 int oracle_fit(int algo, const double *X, int M, int N, int K, double tol, int max_iter,
                int center, const int *iters_lock, int storage,
+               const double *ws_net, const double *ws_G, int *ws_choice, double *ws_rho,
                double *T, double *P, double *lambda, int *iters, double *R, int *found)
 {
     if (!X || !T || !P || !lambda || !iters || !R || !found)
@@ -398,6 +416,11 @@ int oracle_fit(int algo, const double *X, int M, int N, int K, double tol, int m
         return OR_INVALID;
     if (storage != 0 && storage != 1)
         return OR_INVALID;
+    if (ws_net && (algo != 1 || !ws_G))
+        return OR_INVALID;
+    if (ws_choice)
+        for (int k = 0; k < K; k++)
+            ws_choice[k] = 0;
     if (iters_lock)
         for (int k = 0; k < K; k++)
             if (iters_lock[k] < 1)
@@ -410,7 +433,8 @@ int oracle_fit(int algo, const double *X, int M, int N, int K, double tol, int m
     double thresh = 64.0 * DBL_EPSILON * frob(R, M, N);
     if (algo == 0)
         return nipals(R, M, N, K, tol, max_iter, iters_lock, thresh, storage, T, P, lambda, iters, found);
-    return gspca(R, M, N, K, tol, max_iter, iters_lock, thresh, storage, T, P, lambda, iters, found);
+    return gspca(R, M, N, K, tol, max_iter, iters_lock, thresh, storage, ws_net, ws_G, ws_choice, ws_rho, T, P,
+                 lambda, iters, found);
 }
 
 /* ------------------------------------------------------- Jacobi eigensolver */
