@@ -73,6 +73,37 @@ typedef enum {
     GSPCA_ERR_NOT_SUPPORTED = 7     /* sizes beyond what this build handles */
 } gspca_status;
 
+/* Learned warm start of GS-PCA.  The paper has no counterpart: it is a
+ * growth direction of the loop of Sec. 2.3, whose start is the residual
+ * column v = R(k).  At the start of component k a small network proposes a
+ * loading p0 from per-column features of the residual R, and the first pass
+ * over R evaluates both starts:
+ *   features of column n: x_n = [c_n, s_n] / rho with c_n = ||R(n)||,
+ *     s_n = G^T R(n) (16 values, G the sketch below), rho^2 = sum_n c_n^2 / N;
+ *     they are computed once per fit from the packed R and then follow every
+ *     deflation (Eq. 3) exactly, at O(16 (M + N)) work per component;
+ *   network (weights shared by all columns): h1 = gelu(W1 x + b1),
+ *     h2 = gelu(W2 h1 + b2), w_n = W3 . h2 + b3, gelu(z) = z (1 + erf(z/sqrt 2))/2,
+ *     p0 = w / ||w||;
+ *   choice: with v_a = R(k) (the paper's start) and v_b = R p0, the loop
+ *     starts from v_b when ||R^T v_b||^2 / ||v_b||^2 > ||R^T v_a||^2 / ||v_a||^2,
+ *     otherwise from v_a, exactly as the paper; the candidate is skipped when
+ *     w is zero or not finite, or R(k) is zero (the zero-column rule applies).
+ * GS-PCA only.  Parameter layout (FP32, GSPCA_WS_PARAMS values): W1 (64 x 17,
+ * row-major), b1 (64), W2 (64 x 64, row-major), b2 (64), W3 (64), b3 (1). */
+#define GSPCA_WS_SKETCH 16
+#define GSPCA_WS_FEATURES 17
+#define GSPCA_WS_PARAMS 5377
+
+typedef struct {
+    const float *net;   /* device: GSPCA_WS_PARAMS network parameters */
+    const float *G;     /* device: sketch, G_rows x 16 row-major (entries drawn by the caller,
+                           N(0, 1/16) in the intended use); a problem of M rows uses rows 0..M-1 */
+    long G_rows;        /* must be >= M of every problem */
+    int *choice;        /* device, nullable (gspca_fit only): K ints, 1 where the learned start
+                           was used, 0 where the paper's start was */
+} gspca_warm_start;
+
 typedef struct {
     int center;             /* gspca_center, default GSPCA_CENTER_NONE */
     const int *iters_lock;  /* host array of K counts, nullable: run exactly iters_lock[k]
@@ -89,6 +120,9 @@ typedef struct {
                                nothing sets, so the wait limit (timeout_s) runs out and the
                                call reports GSPCA_ERR_TIMEOUT; exercises the timeout path
                                without a fault */
+    const gspca_warm_start *warm;  /* host pointer, nullable: learned warm start (GS-PCA only;
+                               gspca_fit, gspca_fit_host, gspca_fit_batched[_async]).  The first
+                               call on a handle that uses it grows the handle's workspace. */
 } gspca_opts;
 
 /* Per-call record of the last fit on a handle (host memory). */
@@ -148,6 +182,8 @@ typedef struct {
     double *lambda;
     int *iters;             /* nullable */
     int *status;            /* nullable: per-problem gspca_status (device int) */
+    int *ws_choice;         /* nullable: K device ints, 1 where the learned start was used
+                               (opts->warm set) */
 } gspca_problem;
 
 /* Fit `count` independent problems (problems[] is a HOST array of
@@ -221,6 +257,34 @@ gspca_status gspca_fit_noalloc(void *stream, const float *X, gspca_layout layout
                                int N, int K, double tol, int max_iter, gspca_algo algo, float *T,
                                float *P, double *lambda, int *iters, float *R_out,
                                const gspca_opts *opts);
+
+/* Learned warm start: features of the columns of R_k = X - T(:, 0:k) P(:, 0:k)^T
+ * (the residual before component k of a finished fit; X column-major, ldx >= M;
+ * T M x >=k and P N x >=k column-major with leading dimensions M and N, as gspca_fit
+ * writes them; k = 0 ignores T and P).  feat (N x 17, row-major) receives
+ * x_n = [||R_k(n)||, G^T R_k(n)] / rho as defined above.  Device pointers; runs on
+ * `stream` without waiting; allocates nothing.  Used to build training data. */
+gspca_status gspca_ws_features(void *stream, const float *X, long ldx, int M, int N, const float *T,
+                               const float *P, int k, const float *G, float *feat);
+
+/* Learned warm start: w[n] = network(feat[n]) for n < count (feat row-major, 17 per
+ * row).  Device pointers; runs on `stream` without waiting; allocates nothing. */
+gspca_status gspca_ws_forward(void *stream, const float *net, const float *feat, long count, float *w);
+
+/* Learned warm start: one training step on a minibatch of ninst instances.  Instance
+ * i owns feature rows offsets[i] .. offsets[i+1]-1 (offsets: device, ninst + 1 ints,
+ * offsets[0] = 0, offsets[ninst] = ncols) and target[] holds its target loading p*
+ * on those rows (unit norm).  Loss of an instance: 1 - (w . p*)^2 / (w . w) (1 with
+ * zero gradient when w = 0); the step minimises the mean over the minibatch with one
+ * Adam update (step t >= 1, bias-corrected, beta1 0.9, beta2 0.999, eps 1e-8) of net
+ * with its moment buffers adam_m, adam_v (GSPCA_WS_PARAMS each, zero before t = 1).
+ * lr = 0 leaves net, adam_m and adam_v unchanged.  loss (device float) and grad
+ * (device, GSPCA_WS_PARAMS) are nullable outputs: the minibatch loss and gradient
+ * before the update.  The handle owns the step's scratch, grown on demand (not under
+ * stream capture).  Runs on `stream` without waiting. */
+gspca_status gspca_ws_train_step(gspca_t h, void *stream, float *net, float *adam_m, float *adam_v, int step,
+                                 float lr, const float *feat, const float *target, const int *offsets,
+                                 int ninst, long ncols, float *loss, float *grad);
 
 /* Record of the last call on h. */
 gspca_status gspca_get_info(gspca_t h, gspca_info *info);

@@ -32,7 +32,9 @@ GSPCA_ERR_NOT_SUPPORTED = 7
 
 EXPORTS = ["gspca_create", "gspca_fit", "gspca_fit_host", "gspca_fit_batched", "gspca_fit_batched_async",
            "gspca_get_info", "gspca_destroy", "gspca_status_string", "gspca_last_cuda_error",
-           "gspca_fit_noalloc"]
+           "gspca_fit_noalloc", "gspca_ws_features", "gspca_ws_forward", "gspca_ws_train_step"]
+
+WS_SKETCH, WS_FEATURES, WS_PARAMS = 16, 17, 5377
 
 _ALGOS = {"nipals": GSPCA_NIPALS, "gs": GSPCA_GS, GSPCA_NIPALS: GSPCA_NIPALS, GSPCA_GS: GSPCA_GS}
 _DTYPES = {"f32": GSPCA_F32, "bf16": GSPCA_BF16, GSPCA_F32: GSPCA_F32, GSPCA_BF16: GSPCA_BF16}
@@ -47,10 +49,16 @@ class GspcaError(RuntimeError):
         super().__init__(msg)
 
 
+class WarmStartC(ctypes.Structure):
+    _fields_ = [("net", ctypes.c_void_p), ("G", ctypes.c_void_p), ("G_rows", ctypes.c_long),
+                ("choice", ctypes.c_void_p)]
+
+
 class Opts(ctypes.Structure):
     _fields_ = [("center", ctypes.c_int), ("iters_lock", ctypes.POINTER(ctypes.c_int)),
                 ("grid_ctas", ctypes.c_int), ("timeout_s", ctypes.c_double),
-                ("cluster_ctas", ctypes.c_int), ("batch_pass", ctypes.c_int), ("test_stall", ctypes.c_int)]
+                ("cluster_ctas", ctypes.c_int), ("batch_pass", ctypes.c_int), ("test_stall", ctypes.c_int),
+                ("warm", ctypes.POINTER(WarmStartC))]
 
 
 class Info(ctypes.Structure):
@@ -64,7 +72,7 @@ class Problem(ctypes.Structure):
     _fields_ = [("X", ctypes.c_void_p), ("ldx", ctypes.c_long), ("M", ctypes.c_int),
                 ("N", ctypes.c_int), ("K", ctypes.c_int), ("T", ctypes.c_void_p),
                 ("P", ctypes.c_void_p), ("lambda_", ctypes.c_void_p), ("iters", ctypes.c_void_p),
-                ("status", ctypes.c_void_p)]
+                ("status", ctypes.c_void_p), ("ws_choice", ctypes.c_void_p)]
 
 
 _lib = None
@@ -89,6 +97,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.gspca_fit_batched_async.argtypes = [vp, vp, ctypes.POINTER(Problem), i, d, i, i, ctypes.POINTER(Opts), vp]
     lib.gspca_fit_noalloc.argtypes = fit_args[1:]
     lib.gspca_fit_noalloc.restype = i
+    lib.gspca_ws_features.argtypes = [vp, vp, l, i, i, vp, vp, i, vp, vp]
+    lib.gspca_ws_forward.argtypes = [vp, vp, vp, l, vp]
+    lib.gspca_ws_train_step.argtypes = [vp, vp, vp, vp, vp, i, ctypes.c_float, vp, vp, vp, i, l, vp, vp]
     lib.gspca_get_info.argtypes = [vp, ctypes.POINTER(Info)]
     lib.gspca_destroy.argtypes = [vp]
     lib.gspca_status_string.argtypes = [i]
@@ -96,7 +107,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.gspca_last_cuda_error.argtypes = []
     lib.gspca_last_cuda_error.restype = ctypes.c_char_p
     for name in ("gspca_create", "gspca_fit", "gspca_fit_host", "gspca_fit_batched",
-                 "gspca_fit_batched_async", "gspca_get_info", "gspca_destroy"):
+                 "gspca_fit_batched_async", "gspca_get_info", "gspca_destroy", "gspca_ws_features",
+                 "gspca_ws_forward", "gspca_ws_train_step"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -116,7 +128,28 @@ def last_cuda_error() -> str:
 gspca_last_cuda_error = last_cuda_error
 
 
-def _opts(center=0, iters_lock=None, grid_ctas=0, timeout_s=0.0, cluster_ctas=0, test_stall=0, batch_pass=0):
+class WarmStart:
+    """Learned warm start: network parameters (GSPCA_WS_PARAMS float32 CUDA values) and the
+    sketch G (rows x 16 float32 CUDA, row-major; a problem of M rows uses the first M)."""
+
+    def __init__(self, net, G):
+        import torch
+
+        if not (isinstance(net, torch.Tensor) and net.is_cuda and net.dtype == torch.float32
+                and net.numel() == WS_PARAMS and net.is_contiguous()):
+            raise TypeError("net must be a contiguous float32 CUDA tensor of 5377 values")
+        if not (isinstance(G, torch.Tensor) and G.is_cuda and G.dtype == torch.float32 and G.dim() == 2
+                and G.shape[1] == WS_SKETCH and G.is_contiguous()):
+            raise TypeError("G must be a contiguous float32 CUDA tensor of shape (rows, 16)")
+        self.net, self.G = net, G
+
+    def c_struct(self, choice=None):
+        return WarmStartC(self.net.data_ptr(), self.G.data_ptr(), self.G.shape[0],
+                          choice.data_ptr() if choice is not None else None)
+
+
+def _opts(center=0, iters_lock=None, grid_ctas=0, timeout_s=0.0, cluster_ctas=0, test_stall=0, batch_pass=0,
+          warm=None):
     o = Opts()
     o.batch_pass = int(batch_pass)
     o.test_stall = int(test_stall)
@@ -128,6 +161,9 @@ def _opts(center=0, iters_lock=None, grid_ctas=0, timeout_s=0.0, cluster_ctas=0,
     if iters_lock is not None:
         keep = (ctypes.c_int * len(iters_lock))(*[int(v) for v in iters_lock])
         o.iters_lock = ctypes.cast(keep, ctypes.POINTER(ctypes.c_int))
+    if warm is not None:
+        o.warm = ctypes.pointer(warm)
+        keep = (keep, warm)
     return o, keep
 
 
@@ -173,12 +209,15 @@ class FitResult:
     R: object
     status: int
     info: dict
+    ws_choice: object = None
 
 
 def gspca_fit(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="gs",
               center: int = 0, iters_lock=None, want_R: bool = False, grid_ctas: int = 0,
-              timeout_s: float = 0.0, stream=None, check: bool = True, test_stall: int = 0) -> FitResult:
-    """Fit K components of X (a float32 CUDA tensor, any 2-D strided layout)."""
+              timeout_s: float = 0.0, stream=None, check: bool = True, test_stall: int = 0,
+              warm: WarmStart | None = None) -> FitResult:
+    """Fit K components of X (a float32 CUDA tensor, any 2-D strided layout).  `warm`: the
+    learned warm start (GS-PCA); the result's ws_choice marks the components that used it."""
     import torch
 
     if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
@@ -196,7 +235,9 @@ def gspca_fit(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="
     R = torch.empty((N, M), device=dev, dtype=torch.float32).t() if want_R else None
     if stream is None:
         stream = torch.cuda.current_stream(dev).cuda_stream
-    o, keep = _opts(center, iters_lock, grid_ctas, timeout_s, 0, test_stall)
+    choice = torch.zeros(K, device=dev, dtype=torch.int32) if warm is not None else None
+    o, keep = _opts(center, iters_lock, grid_ctas, timeout_s, 0, test_stall,
+                    warm=warm.c_struct(choice) if warm is not None else None)
     st = load().gspca_fit(ctypes.c_void_p(h), ctypes.c_void_p(stream), ctypes.c_void_p(X.data_ptr()),
                           layout, int(ldx), M, N, int(K), float(tol), int(max_iter), _ALGOS[algo],
                           ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(P.data_ptr()),
@@ -205,7 +246,7 @@ def gspca_fit(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="
     del keep
     if check and st not in (GSPCA_OK, GSPCA_WARN_NOT_CONVERGED, GSPCA_ERR_DEGENERATE):
         raise GspcaError(st, "gspca_fit")
-    return FitResult(T, P, lam, iters, R, st, gspca_get_info(h))
+    return FitResult(T, P, lam, iters, R, st, gspca_get_info(h), choice)
 
 
 def gspca_fit_host(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="gs",
@@ -318,11 +359,13 @@ class Batch:
             lam = torch.zeros(K, device=dev, dtype=torch.float64)
             iters = torch.zeros(K, device=dev, dtype=torch.int32)
             st = torch.full((1,), -1, device=dev, dtype=torch.int32)
+            ch = torch.zeros(K, device=dev, dtype=torch.int32)
             d = self.descs[i]
             d.X, d.ldx, d.M, d.N, d.K = X.data_ptr(), int(ldx), M, N, K
             d.T, d.P, d.lambda_, d.iters, d.status = (T.data_ptr(), P.data_ptr(), lam.data_ptr(),
                                                       iters.data_ptr(), st.data_ptr())
-            self.outs.append(FitResult(T, P, lam, iters, None, st, {}))
+            d.ws_choice = ch.data_ptr()
+            self.outs.append(FitResult(T, P, lam, iters, None, st, {}, ch))
 
     def __len__(self):
         return len(self.outs)
@@ -334,7 +377,7 @@ class Batch:
 
 def gspca_fit_batched(h: int, problems, tol: float = 1e-6, max_iter: int = 1000, algo="gs",
                       cluster_ctas: int = 0, timeout_s: float = 0.0, stream=None, check: bool = True,
-                      test_stall: int = 0, batch_pass: int = 0):
+                      test_stall: int = 0, batch_pass: int = 0, warm: WarmStart | None = None):
     """Fit independent problems in one persistent launch (per 256 problems) and wait.
     `problems` is a Batch or a list accepted by Batch; returns (Batch, worst status)."""
     import torch
@@ -342,7 +385,8 @@ def gspca_fit_batched(h: int, problems, tol: float = 1e-6, max_iter: int = 1000,
     b = problems if isinstance(problems, Batch) else Batch(problems)
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
-    o, _ = _opts(0, None, 0, timeout_s, cluster_ctas, test_stall, batch_pass)
+    o, _keep = _opts(0, None, 0, timeout_s, cluster_ctas, test_stall, batch_pass,
+                     warm=warm.c_struct() if warm is not None else None)
     st = load().gspca_fit_batched(ctypes.c_void_p(h), ctypes.c_void_p(stream), b.descs, len(b),
                                   float(tol), int(max_iter), _ALGOS[algo], ctypes.byref(o))
     if check and st not in (GSPCA_OK, GSPCA_WARN_NOT_CONVERGED, GSPCA_ERR_DEGENERATE):
@@ -355,7 +399,7 @@ def gspca_fit_batched(h: int, problems, tol: float = 1e-6, max_iter: int = 1000,
 
 def gspca_fit_batched_async(h: int, batch: Batch, tol: float = 1e-6, max_iter: int = 1000, algo="gs",
                             cluster_ctas: int = 0, timeout_s: float = 0.0, worst=None, stream=None,
-                            batch_pass: int = 0) -> int:
+                            batch_pass: int = 0, warm: WarmStart | None = None) -> int:
     """Enqueue a batch without waiting (usable inside CUDA stream capture after one uncaptured
     call on the same shapes).  `worst` is an optional 1-element int32 CUDA tensor that receives
     the worst per-problem status.  Returns the enqueue status."""
@@ -363,7 +407,8 @@ def gspca_fit_batched_async(h: int, batch: Batch, tol: float = 1e-6, max_iter: i
 
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
-    o, _ = _opts(0, None, 0, timeout_s, cluster_ctas, 0, batch_pass)
+    o, _keep = _opts(0, None, 0, timeout_s, cluster_ctas, 0, batch_pass,
+                     warm=warm.c_struct() if warm is not None else None)
     return load().gspca_fit_batched_async(ctypes.c_void_p(h), ctypes.c_void_p(stream), batch.descs, len(batch),
                                           float(tol), int(max_iter), _ALGOS[algo], ctypes.byref(o),
                                           ctypes.c_void_p(worst.data_ptr()) if worst is not None else None)
@@ -407,3 +452,58 @@ def gspca_fit_noalloc(X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="
     if check and st not in (GSPCA_OK, GSPCA_WARN_NOT_CONVERGED, GSPCA_ERR_DEGENERATE):
         raise GspcaError(st, "gspca_fit_noalloc")
     return FitResult(T, P, lam, iters, R, st, {})
+
+
+# ------------------------------------------------------------------ learned warm start
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream, dev=None):
+    import torch
+
+    return stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+
+
+def gspca_ws_features(X, G, T=None, P=None, k: int = 0, out=None, stream=None):
+    """Features (N x 17 float32 CUDA) of the columns of R_k = X - T[:, :k] P[:, :k]^T; X column-major
+    float32 CUDA (a transposed contiguous tensor), T and P as gspca_fit returns them."""
+    import torch
+
+    M, N = X.shape
+    if X.stride(0) != 1:
+        raise TypeError("X must be column-major")
+    for t in (T, P):
+        if t is not None and not (t.stride(0) == 1 and t.stride(1) == t.shape[0]):
+            raise TypeError("T and P must be column-major with leading dimension = rows")
+    feat = out if out is not None else torch.empty((N, WS_FEATURES), device=X.device, dtype=torch.float32)
+    st = load().gspca_ws_features(ctypes.c_void_p(_stream(stream, X.device)), _ptr(X), int(X.stride(1)), M, N,
+                                  _ptr(T) if k > 0 else None, _ptr(P) if k > 0 else None, int(k), _ptr(G),
+                                  _ptr(feat))
+    if st != GSPCA_OK:
+        raise GspcaError(st, "gspca_ws_features")
+    return feat
+
+
+def gspca_ws_forward(net, feat, out=None, stream=None):
+    """Network output for every feature row (float32 CUDA)."""
+    import torch
+
+    w = out if out is not None else torch.empty(feat.shape[0], device=feat.device, dtype=torch.float32)
+    st = load().gspca_ws_forward(ctypes.c_void_p(_stream(stream, feat.device)), _ptr(net), _ptr(feat),
+                                 int(feat.shape[0]), _ptr(w))
+    if st != GSPCA_OK:
+        raise GspcaError(st, "gspca_ws_forward")
+    return w
+
+
+def gspca_ws_train_step(h: int, net, m, v, step: int, lr: float, feat, target, offsets, loss=None, grad=None,
+                        stream=None):
+    """One Adam step of the network on the instances delimited by `offsets` (int32 CUDA)."""
+    st = load().gspca_ws_train_step(ctypes.c_void_p(h), ctypes.c_void_p(_stream(stream, feat.device)), _ptr(net),
+                                    _ptr(m), _ptr(v), int(step), float(lr), _ptr(feat), _ptr(target),
+                                    _ptr(offsets), int(offsets.numel() - 1), int(feat.shape[0]), _ptr(loss),
+                                    _ptr(grad))
+    if st != GSPCA_OK:
+        raise GspcaError(st, "gspca_ws_train_step")

@@ -25,7 +25,7 @@ const void* batch_kernel_for(gspca_dtype dt) {
     return dt == GSPCA_BF16 ? batch_kernel_ptr<__nv_bfloat16>() : batch_kernel_ptr<float>();
 }
 
-cudaError_t plan_batch(int device, gspca_dtype dt, int C, long maxM, int maxN, int maxK, BatchPlan* bp) {
+cudaError_t plan_batch(int device, gspca_dtype dt, int C, long maxM, int maxN, int maxK, bool warm, BatchPlan* bp) {
     const void* kern = batch_kernel_for(dt);
     cudaFuncAttributes fa{};
     cudaError_t e = cudaFuncGetAttributes(&fa, kern);
@@ -39,7 +39,7 @@ cudaError_t plan_batch(int device, gspca_dtype dt, int C, long maxM, int maxN, i
     // The same dynamic size for every team size (the kernel attribute is set once
     // per plan and plans are cached): the ring takes what the vectors leave.
     const long dyn = ((long)optin - (long)fa.sharedSizeBytes - 1024) / 128 * 128;
-    const long vec = (long)sizeof(float) * (2L * bp->ldk + bp->max_slice);
+    const long vec = (long)sizeof(float) * (2L * bp->ldk + 2L * bp->max_slice);
     const long ring = (dyn - vec) / 128 * 128;
     if (ring < kLdsBytes) return cudaErrorInvalidConfiguration;  // the warp-group pass needs its stages
     bp->ring_bytes = (int)ring;
@@ -65,22 +65,23 @@ cudaError_t plan_batch(int device, gspca_dtype dt, int C, long maxM, int maxN, i
     if ((e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg)) != cudaSuccess) return e;
     if (n < 1) return cudaErrorInvalidConfiguration;
     bp->clusters = n;
-    bp->dims = WsDims{(maxM + 3) / 4 * 4, maxN, maxK, C};
+    bp->dims = WsDims{(maxM + 3) / 4 * 4, maxN, maxK, C, warm};
     bp->stride = align_up(carve(nullptr, bp->dims).bytes, 256);
     return cudaSuccess;
 }
 
 // plan_batch through the handle's cache (a captured call finds its plan there
 // and makes no attribute or occupancy query).
-cudaError_t cached_plan(gspca_t h, int C, long maxM, int maxN, int maxK, BatchPlan* bp) {
-    const uint64_t key = ((uint64_t)C << 58) ^ ((uint64_t)maxM << 24) ^ ((uint64_t)maxN << 8) ^ (uint64_t)maxK;
+cudaError_t cached_plan(gspca_t h, int C, long maxM, int maxN, int maxK, bool warm, BatchPlan* bp) {
+    const uint64_t key = ((uint64_t)C << 58) ^ ((uint64_t)warm << 57) ^ ((uint64_t)maxM << 24) ^
+                         ((uint64_t)maxN << 8) ^ (uint64_t)maxK;
     auto it = h->batch.plans.find(key);
     if (it != h->batch.plans.end() && it->second.C == C && it->second.dims.N == maxN && it->second.dims.K == maxK &&
-        it->second.dims.Mp == (maxM + 3) / 4 * 4) {
+        it->second.dims.Mp == (maxM + 3) / 4 * 4 && it->second.dims.warm == warm) {
         *bp = it->second;
         return cudaSuccess;
     }
-    const cudaError_t e = plan_batch(h->device, h->dtype, C, maxM, maxN, maxK, bp);
+    const cudaError_t e = plan_batch(h->device, h->dtype, C, maxM, maxN, maxK, warm, bp);
     if (e == cudaSuccess) h->batch.plans[key] = *bp;
     return e;
 }
@@ -91,7 +92,7 @@ bool capturing(cudaStream_t s) {
     return cs != cudaStreamCaptureStatusNone;
 }
 
-uint64_t shape_key(const gspca_problem* p, int count, int algo) {
+uint64_t shape_key(const gspca_problem* p, int count, int algo, bool warm) {
     uint64_t h = 1469598103934665603ull;
     auto mix = [&](uint64_t v) {
         h ^= v;
@@ -99,6 +100,7 @@ uint64_t shape_key(const gspca_problem* p, int count, int algo) {
     };
     mix((uint64_t)count);
     mix((uint64_t)algo);
+    mix((uint64_t)warm);
     for (int i = 0; i < count; ++i) {
         mix((uint64_t)p[i].M);
         mix((uint64_t)p[i].N);
@@ -118,6 +120,12 @@ gspca_status check_batch(gspca_t h, const gspca_problem* p, int count, double to
         const int c = opts->cluster_ctas;
         if (c != 0 && c != 1 && c != 2 && c != 4 && c != 8 && c != 16) return GSPCA_ERR_INVALID_ARG;
         if (opts->batch_pass < 0 || opts->batch_pass > 2) return GSPCA_ERR_INVALID_ARG;
+        if (opts->warm) {
+            if (!opts->warm->net || !opts->warm->G) return GSPCA_ERR_INVALID_ARG;
+            if (algo != GSPCA_GS) return GSPCA_ERR_NOT_SUPPORTED;
+            for (int i = 0; i < count; ++i)
+                if (p[i].M > opts->warm->G_rows) return GSPCA_ERR_INVALID_ARG;
+        }
     }
     for (int i = 0; i < count; ++i) {
         const gspca_problem& q = p[i];
@@ -187,6 +195,8 @@ gspca_status enqueue_batch(gspca_t h, cudaStream_t s, const gspca_problem* p, in
     h->batch.timing_dev = timing_dev;
 #endif
     a->stall = (opts && opts->test_stall) ? 1 : 0;
+    a->ws_net = (opts && opts->warm) ? opts->warm->net : nullptr;
+    a->ws_G = (opts && opts->warm) ? opts->warm->G : nullptr;
     a->pass = pass;
     a->ws = carve(b.ws, bp.dims);
     a->ws_stride = bp.stride;
@@ -218,6 +228,7 @@ gspca_status enqueue_batch(gspca_t h, cudaStream_t s, const gspca_problem* p, in
             d.lambda = q.lambda;
             d.iters = q.iters;
             d.status = q.status;
+            d.ws_choice = q.ws_choice;
             d.ldx = q.ldx;
             d.M = q.M;
             d.N = q.N;
@@ -239,16 +250,17 @@ gspca_status choose_team(gspca_t h, cudaStream_t s, const gspca_problem* p, int 
                          gspca_algo algo, const gspca_opts* opts, long maxM, int maxN, int maxK, bool cap,
                          BatchPlan* out, int* pass) {
     const int fc = opts ? opts->cluster_ctas : 0, fp = opts ? opts->batch_pass : 0;
+    const bool warm = opts && opts->warm;
     if (fc && fp) {
         *pass = fp;
-        GS_CUDA(cached_plan(h, fc, maxM, maxN, maxK, out));
+        GS_CUDA(cached_plan(h, fc, maxM, maxN, maxK, warm, out));
         return ensure_workspace(h, *out, !cap);
     }
-    const uint64_t key = shape_key(p, count, (int)algo) ^ ((uint64_t)fc << 40) ^ ((uint64_t)fp << 48);
+    const uint64_t key = shape_key(p, count, (int)algo, warm) ^ ((uint64_t)fc << 40) ^ ((uint64_t)fp << 48);
     auto it = h->batch.tuned.find(key);
     if (it != h->batch.tuned.end()) {
         *pass = it->second & 3;
-        GS_CUDA(cached_plan(h, it->second >> 2, maxM, maxN, maxK, out));
+        GS_CUDA(cached_plan(h, it->second >> 2, maxM, maxN, maxK, warm, out));
         return ensure_workspace(h, *out, !cap);
     }
     if (cap) return GSPCA_ERR_NOT_SUPPORTED;
@@ -258,7 +270,7 @@ gspca_status choose_team(gspca_t h, cudaStream_t s, const gspca_problem* p, int 
     int best = 0;
     for (int C : teams) {
         BatchPlan bp{};
-        if (cached_plan(h, C, maxM, maxN, maxK, &bp) != cudaSuccess) {
+        if (cached_plan(h, C, maxM, maxN, maxK, warm, &bp) != cudaSuccess) {
             cudaGetLastError();  // an infeasible cluster shape is skipped
             continue;
         }
@@ -280,7 +292,7 @@ gspca_status choose_team(gspca_t h, cudaStream_t s, const gspca_problem* p, int 
     if (best == 0) return GSPCA_ERR_NOT_SUPPORTED;
     h->batch.tuned[key] = best;
     *pass = best & 3;
-    GS_CUDA(cached_plan(h, best >> 2, maxM, maxN, maxK, out));
+    GS_CUDA(cached_plan(h, best >> 2, maxM, maxN, maxK, warm, out));
     return ensure_workspace(h, *out, true);
 }
 

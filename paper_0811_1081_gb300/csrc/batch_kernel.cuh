@@ -24,6 +24,7 @@ struct BatchProblem {
     double* lambda;  // K
     int* iters;      // K, nullable
     int* status;     // nullable
+    int* ws_choice;  // K, nullable (learned warm start)
     long long ldx;
     int M, N, K;
     int pad;
@@ -54,6 +55,8 @@ struct BatchArgs {
     int stall;  // testing hook: ring waits first wait for ctl->never
     int pass;   // 1: pass_warp (no ring), 2: the CTA-wide ring passes
     unsigned long long* timing;  // phase times of problem 0 (instrumented builds), nullable
+    const float* ws_net;  // learned warm start (GS-PCA), nullable: network parameters
+    const float* ws_G;    // its sketch (rows >= every problem's M, 16 per row)
     BatchCtl* ctl;
     int* queue;  // this launch's word of ctl->queue
     // cluster 0's workspace; cluster c adds c * ws_stride bytes to every pointer
@@ -254,6 +257,16 @@ __global__ void __launch_bounds__(kBlock, 1) batch_kernel(const __grid_constant_
             f.max_slice = a.max_slice;
             f.redundant_max = a.redundant_max;
             f.stall_word = a.stall ? &a.ctl->never : nullptr;
+            if (a.ws_net) {
+                f.ws_net = a.ws_net;
+                f.ws_G = a.ws_G;
+                f.wsF = shift(a.ws.wsF, off);
+                f.wsP0 = shift(a.ws.wsP0, off);
+                f.pC = shift(a.ws.pC, off);
+                f.wsPart = shift(a.ws.wsPart, off);
+                f.wsInit = shift(a.ws.wsInit, off);
+                f.ws_choice = pb.ws_choice;
+            }
             fa = f;
         }
         __syncthreads();

@@ -35,6 +35,7 @@
 #pragma once
 
 #include "device_common.cuh"
+#include "warmstart.cuh"
 
 namespace gspca {
 
@@ -85,6 +86,15 @@ struct FitArgs {
     int max_slice;            // shared-memory length of the N slice (>= n1 - n0)
     int redundant_max;        // reduce k-vectors in every CTA when k <= this
     int narrow;               // 1: the loading pass is pass_lds (N <= 1024, no CTA ring)
+    // learned warm start (GS-PCA; all null when off)
+    const float* ws_net;      // kWsParams network parameters
+    const float* ws_G;        // sketch, M x 16 row-major
+    float* wsF;               // N x 17: squared norm and sketch of every column of the current residual
+    float* wsP0;              // N: network output for the current component
+    float* pC;                // G x N: CTA partials of R^T v_b (the learned candidate)
+    float* wsPart;            // G x 32: CTA partials of the per-component feature update
+    float* wsInit;            // G x 17 x N: CTA partials of the initial sketch
+    int* ws_choice;           // K, nullable: 1 where the learned start was used
     const int* stall_word;    // testing, nullable: a word nothing sets; the first ring wait of
                               // every pass first waits for it (bounded) and so runs out
 };
@@ -100,6 +110,7 @@ struct __align__(16) SmemFit {
     ff sff[4];
     ff lamff;
     double dsc[4];
+    double wsv[24];
     unsigned long long mbar[kMaxStages];
     int flag;
     int sel;
@@ -1053,6 +1064,289 @@ struct FitOutcome {
     bool alive;  // false: a bounded wait gave up, the kernel must leave
 };
 
+// ------------------------------------------------------------------ learned warm start
+
+// Sketch of the initial residual.  Every CTA accumulates, for every column, the
+// squared norm and the 16 sketch sums G^T R(n) over its own panels (a thread
+// per column, rows in order), writes them to wsInit[g][j][n]; after the team
+// barrier each CTA sums its column slice over the team in CTA order into wsF.
+// Returns false if the barrier failed.
+template <class E, class Team>
+__device__ __noinline__ bool ws_sketch_init(const FitArgs& f, const Team& tm, SmemFit& sm, unsigned& epoch, int p0,
+                                            int p1, int n0, int n1) {
+    const int tid = threadIdx.x, T = blockDim.x, N = f.N;
+    for (int c = tid; c < N; c += T) {
+        float acc[kWsIn];
+#pragma unroll
+        for (int j = 0; j < kWsIn; ++j) acc[j] = 0.f;
+        for (int p = p0; p < p1; ++p) {
+            const float4 d = Cell<E>::ldg(f.R, (size_t)p * f.ldp + c);
+            const float v4[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = 4 * p + q;
+                if (row >= f.M) break;
+                const float v = v4[q];
+                acc[0] = fmaf(v, v, acc[0]);
+                const float4* g4 = reinterpret_cast<const float4*>(f.ws_G + (size_t)row * kWsSketch);
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const float4 gg = __ldg(g4 + h);
+                    acc[1 + 4 * h] = fmaf(gg.x, v, acc[1 + 4 * h]);
+                    acc[2 + 4 * h] = fmaf(gg.y, v, acc[2 + 4 * h]);
+                    acc[3 + 4 * h] = fmaf(gg.z, v, acc[3 + 4 * h]);
+                    acc[4 + 4 * h] = fmaf(gg.w, v, acc[4 + 4 * h]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kWsIn; ++j) f.wsInit[((size_t)tm.g * kWsIn + j) * N + c] = acc[j];
+    }
+    if (!tm.sync(epoch, &sm.flag)) return false;
+    const int nc = n1 - n0;
+    for (int e = tid; e < nc * kWsIn; e += T) {
+        const int n = n0 + e / kWsIn, j = e % kWsIn;
+        float t = 0.f;
+        for (int g2 = 0; g2 < tm.G; ++g2) t += ldcg(f.wsInit + ((size_t)g2 * kWsIn + j) * N + n);
+        f.wsF[(size_t)n * kWsIn + j] = t;
+    }
+    return true;
+}
+
+// Features and network output for component k (GS-PCA).  For k > 0 the
+// features first follow the deflation of component k-1, R_k = R_{k-1} -
+// lambda v u^T (Eq. 3), exactly:
+//   s_n <- s_n - lambda (G^T v) u_n,
+//   c_n^2 <- c_n^2 - 2 lambda u_n (R_{k-1}^T v)_n + lambda^2 u_n^2,
+// with (R_{k-1}^T v)_n = upre_n / ||v' - V b'|| from the last pass of k-1 and
+// G^T v summed over the team.  rho^2 = sum c_n^2 / N follows the same update.
+// Then a warp per column of this CTA's slice evaluates the network on
+// x_n = [c_n, s_n] / rho and writes wsP0; *ww receives ||w||^2 over the team.
+// Two team barriers.  Returns false if one failed.
+template <class Team>
+__device__ __noinline__ bool ws_prepare(const FitArgs& f, const Team& tm, SmemFit& sm, unsigned& epoch, int k,
+                                        int r0, int r1, int n0, int n1, double lam_prev, float vinv_prev,
+                                        double* ww) {
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+    float* wp = f.wsPart + (size_t)tm.g * 32;
+    if (k > 0)  // G^T v_{k-1} over this CTA's rows
+        rows_times_matrix(f.ws_G, kWsSketch, r0, r1, kWsSketch,
+                          [&](int r) { return f.V[(size_t)r * f.ldv + (k - 1)]; }, wp, sm);
+    ff a0 = ff_zero(), a1 = ff_zero(), a2 = ff_zero();
+    for (int n = n0 + tid; n < n1; n += T) {
+        a0 = ff_add(a0, ff{f.wsF[(size_t)n * kWsIn], 0.f});
+        if (k > 0) {
+            const float u = f.U[(size_t)n * f.ldu + (k - 1)];
+            a1 = ff_add(a1, ff_mul_ff(u, f.upre[n] * vinv_prev));
+            a2 = ff_add(a2, ff_sqr(u));
+        }
+    }
+    a0 = block_sum_ff(a0, sm);
+    a1 = block_sum_ff(a1, sm);
+    a2 = block_sum_ff(a2, sm);
+    if (tid == 0) {
+        wp[16] = a0.hi;
+        wp[17] = a0.lo;
+        wp[18] = a1.hi;
+        wp[19] = a1.lo;
+        wp[20] = a2.hi;
+        wp[21] = a2.lo;
+    }
+    if (!tm.sync(epoch, &sm.flag)) return false;
+    if (tid < 22) {  // sums over the team, CTA order
+        double t = 0.0;
+        for (int g2 = 0; g2 < tm.G; ++g2) t += (double)ldcg(f.wsPart + (size_t)g2 * 32 + tid);
+        sm.wsv[tid] = t;
+    }
+    __syncthreads();
+    const double lam = lam_prev;
+    double rho2 = sm.wsv[16] + sm.wsv[17];
+    if (k > 0) {
+        rho2 += -2.0 * lam * (sm.wsv[18] + sm.wsv[19]) + lam * lam * (sm.wsv[20] + sm.wsv[21]);
+        const float lamf = (float)lam;
+        for (int n = n0 + tid; n < n1; n += T) {
+            const float u = f.U[(size_t)n * f.ldu + (k - 1)];
+            float* x = f.wsF + (size_t)n * kWsIn;
+            const float rv = f.upre[n] * vinv_prev;
+            x[0] = fmaf(lamf * u, fmaf(lamf, u, -2.f * rv), x[0]);
+#pragma unroll
+            for (int j = 0; j < kWsSketch; ++j) x[1 + j] = fmaf(-lamf * (float)sm.wsv[j], u, x[1 + j]);
+        }
+        __syncthreads();
+    }
+    rho2 /= (double)f.N;
+    const float invrho = rho2 > 0.0 ? (float)(1.0 / sqrt(rho2)) : 0.f;
+    ff my = ff_zero();
+    for (int n = n0 + warp; n < n1; n += nw) {
+        const float* xr = f.wsF + (size_t)n * kWsIn;
+        float x[kWsIn];
+        x[0] = sqrtf(fmaxf(xr[0], 0.f)) * invrho;
+#pragma unroll
+        for (int j = 1; j < kWsIn; ++j) x[j] = xr[j] * invrho;
+        const float w = ws_forward_warp(f.ws_net, x, lane);
+        if (lane == 0) {
+            f.wsP0[n] = w;
+            my = ff_add(my, ff_sqr(w));
+        }
+    }
+    my = block_sum_ff(my, sm);
+    if (tid == 0) {
+        wp[22] = my.hi;
+        wp[23] = my.lo;
+    }
+    if (!tm.sync(epoch, &sm.flag)) return false;
+    if (tid == 0) {
+        double t = 0.0;
+        for (int g2 = 0; g2 < tm.G; ++g2)
+            t += (double)ldcg(f.wsPart + (size_t)g2 * 32 + 22) + (double)ldcg(f.wsPart + (size_t)g2 * 32 + 23);
+        sm.wsv[22] = t;
+    }
+    __syncthreads();
+    *ww = sm.wsv[22];
+    return true;
+}
+
+// The first pass of component k with both starts (learned candidate on):
+// deflation of component k-1 as in row_pass<kPassCol>, the paper's start
+// v_a = R(kcol) and the candidate v_b = R p0 (p0 = wsP0 / sqrt(ww)) row by row,
+// and s_a = R^T v_a (-> pA), s_b = R^T v_b (-> pC) while the panel is in
+// registers.  *sa / *sb receive ||v_a||^2 / ||v_b||^2 over the CTA's rows.
+template <int CPT, class E>
+__device__ __noinline__ void ws_start_pass(const FitArgs& f, SmemFit& sm, int g, int p0, int p1, int kcol,
+                                           bool deflate, float lamf, int kprev, int buf, float inv_nu, double ww,
+                                           float* pA, ff* sa, ff* sb) {
+    constexpr int PPR = PassShape<CPT>::PPR;
+    constexpr int RPR = PassShape<CPT>::RPR;
+    constexpr int SH = 5 - Log2<RPR>::value;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int T = blockDim.x, N = f.N;
+    const size_t ldp = (size_t)f.ldp;
+    const float pscale = (float)(1.0 / sqrt(ww));
+    float uc[CPT], pc[CPT], acc_a[CPT], acc_b[CPT];
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+        const int c = tid + i * T;
+        uc[i] = (deflate && c < N) ? ldcg(f.ut + (size_t)buf * N + c) * inv_nu : 0.f;
+        pc[i] = c < N ? ldcg(f.wsP0 + c) * pscale : 0.f;
+        acc_a[i] = acc_b[i] = 0.f;
+    }
+    int owner = -1;
+    if ((kcol % T) == tid) owner = kcol / T;
+    ff my_a = ff_zero(), my_b = ff_zero();
+    int bsel = 0;
+    for (int pb = p0; pb < p1; pb += PPR, bsel ^= 1) {
+        float4 d[PPR][CPT];
+#pragma unroll
+        for (int pp = 0; pp < PPR; ++pp) {
+            const int p = pb + pp;
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) {
+                const int c = tid + i * T;
+                d[pp][i] = (p < p1 && c < N) ? Cell<E>::ldg(f.R, (size_t)p * ldp + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        if (deflate) {
+#pragma unroll
+            for (int pp = 0; pp < PPR; ++pp) {
+                const int p = pb + pp;
+                float cf[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int row = 4 * p + q;
+                    cf[q] = (p < p1 && row < f.M) ? lamf * f.V[(size_t)row * f.ldv + kprev] : 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < CPT; ++i) {
+                    const int c = tid + i * T;
+                    float4 v = d[pp][i];
+                    v.x = fmaf(-cf[0], uc[i], v.x);
+                    v.y = fmaf(-cf[1], uc[i], v.y);
+                    v.z = fmaf(-cf[2], uc[i], v.z);
+                    v.w = fmaf(-cf[3], uc[i], v.w);
+                    v = Cell<E>::quant(v);
+                    d[pp][i] = v;
+                    if (p < p1 && c < N) Cell<E>::stg(f.R, (size_t)p * ldp + c, v);
+                }
+            }
+        }
+        // v_b rows: warp butterflies, then the warp partials through shared memory
+        float acc[RPR];
+#pragma unroll
+        for (int r = 0; r < RPR; ++r) acc[r] = 0.f;
+#pragma unroll
+        for (int i = 0; i < CPT; ++i)
+#pragma unroll
+            for (int pp = 0; pp < PPR; ++pp) {
+                acc[pp * 4 + 0] = fmaf(d[pp][i].x, pc[i], acc[pp * 4 + 0]);
+                acc[pp * 4 + 1] = fmaf(d[pp][i].y, pc[i], acc[pp * 4 + 1]);
+                acc[pp * 4 + 2] = fmaf(d[pp][i].z, pc[i], acc[pp * 4 + 2]);
+                acc[pp * 4 + 3] = fmaf(d[pp][i].w, pc[i], acc[pp * 4 + 3]);
+            }
+        const float r = warp_multi_reduce<RPR>(acc, lane);
+        if ((lane & ((1 << SH) - 1)) == 0) sm.wsum[bsel][warp][lane >> SH] = r;
+        // v_a rows: the owner of column kcol publishes them
+        if (owner >= 0) {
+#pragma unroll
+            for (int pp = 0; pp < PPR; ++pp) {
+                float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < CPT; ++i)
+                    if (i == owner) x = d[pp][i];
+                sm.vrow[bsel][pp * 4 + 0] = x.x;
+                sm.vrow[bsel][pp * 4 + 1] = x.y;
+                sm.vrow[bsel][pp * 4 + 2] = x.z;
+                sm.vrow[bsel][pp * 4 + 3] = x.w;
+                my_a = ff_add(my_a, ff_sqr(x.x));
+                my_a = ff_add(my_a, ff_sqr(x.y));
+                my_a = ff_add(my_a, ff_sqr(x.z));
+                my_a = ff_add(my_a, ff_sqr(x.w));
+            }
+        }
+        __syncthreads();
+        float rs = 0.f;
+        if (lane < RPR)
+            for (int w = 0; w < nw; ++w) rs += sm.wsum[bsel][w][lane];
+        if (warp == 0 && lane < RPR && pb + (lane >> 2) < p1) my_b = ff_add(my_b, ff_sqr(rs));
+        float ra[RPR], rb[RPR];
+#pragma unroll
+        for (int r2 = 0; r2 < RPR; ++r2) {
+            rb[r2] = __shfl_sync(kFull, rs, r2);
+            ra[r2] = sm.vrow[bsel][r2];
+        }
+#pragma unroll
+        for (int i = 0; i < CPT; ++i)
+#pragma unroll
+            for (int pp = 0; pp < PPR; ++pp) {
+                const float4 v = d[pp][i];
+                acc_a[i] = fmaf(v.x, ra[pp * 4 + 0], acc_a[i]);
+                acc_a[i] = fmaf(v.y, ra[pp * 4 + 1], acc_a[i]);
+                acc_a[i] = fmaf(v.z, ra[pp * 4 + 2], acc_a[i]);
+                acc_a[i] = fmaf(v.w, ra[pp * 4 + 3], acc_a[i]);
+                acc_b[i] = fmaf(v.x, rb[pp * 4 + 0], acc_b[i]);
+                acc_b[i] = fmaf(v.y, rb[pp * 4 + 1], acc_b[i]);
+                acc_b[i] = fmaf(v.z, rb[pp * 4 + 2], acc_b[i]);
+                acc_b[i] = fmaf(v.w, rb[pp * 4 + 3], acc_b[i]);
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+        const int c = tid + i * T;
+        if (c < N) {
+            pA[c] = acc_a[i];
+            f.pC[(size_t)g * N + c] = acc_b[i];
+        }
+    }
+    if (warp == 0) {
+        const ff t = warp_sum_ff(my_b);
+        if (lane == 0) sm.sff[3] = t;
+    }
+    if (owner >= 0) sm.ffg[0] = my_a;  // kcol < N: exactly one thread owns it
+    __syncthreads();
+    *sa = sm.ffg[0];
+    *sb = sm.sff[3];
+    __syncthreads();
+}
+
 // (Re)initialise this CTA's ring: S stages of ppr panels of panel_bytes each.
 // Must be called with no copy in flight.
 __device__ __forceinline__ void ring_setup(Ring& rg, SmemFit& sm, unsigned char* dyn_smem, int S, int ppr,
@@ -1128,24 +1422,47 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
         PHASE_MARK(0);
         const bool defl = k > 0;
         const float lamf = gs ? (float)lam_prev : 1.f;
-#pragma unroll
-        for (int i = 0; i < CPT; ++i) {
-            const int c = tid + i * T;
-            uc[i] = (defl && c < N) ? ldcg(f.ut + (size_t)buf * N + c) * inv_nu : 0.f;
-        }
-        if (!row_pass<CPT, kPassCol, E>(f, sm, rg, p0, p1, uc, k, defl, lamf, k - 1, sacc, sc)) {
-            if (tm.fail(f)) {
+        // learned warm start: features, network output, and a first pass with both starts
+        const bool wsk = gs && f.ws_net != nullptr;
+        bool cand = false;
+        if (wsk) {
+            if (k == 0 && !ws_sketch_init<E>(f, tm, sm, epoch, p0, p1, n0, n1)) {
                 alive = false;
                 goto leave;
             }
-            sc = ff{__int_as_float(0x7fc00000), 0.f};
+            double ww = 0.0;
+            if (!ws_prepare(f, tm, sm, epoch, k, r0, r1, n0, n1, lam_prev, vinv_prev, &ww)) {
+                alive = false;
+                goto leave;
+            }
+            cand = ww > 0.0 && isfinite(ww);
+            if (cand) {
+                ff sa, sb;
+                ws_start_pass<CPT, E>(f, sm, g, p0, p1, k, defl, lamf, k - 1, buf, inv_nu, ww, pA, &sa, &sb);
+                write_scalar(f, g, 0, sa);
+                write_scalar(f, g, 1, sb);
+            }
         }
+        if (!cand) {
 #pragma unroll
-        for (int i = 0; i < CPT; ++i) {
-            const int c = tid + i * T;
-            if (c < N) pA[c] = sacc[i];
+            for (int i = 0; i < CPT; ++i) {
+                const int c = tid + i * T;
+                uc[i] = (defl && c < N) ? ldcg(f.ut + (size_t)buf * N + c) * inv_nu : 0.f;
+            }
+            if (!row_pass<CPT, kPassCol, E>(f, sm, rg, p0, p1, uc, k, defl, lamf, k - 1, sacc, sc)) {
+                if (tm.fail(f)) {
+                    alive = false;
+                    goto leave;
+                }
+                sc = ff{__int_as_float(0x7fc00000), 0.f};
+            }
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) {
+                const int c = tid + i * T;
+                if (c < N) pA[c] = sacc[i];
+            }
+            write_scalar(f, g, 0, sc);
         }
-        write_scalar(f, g, 0, sc);
         if (gs && k > 0)  // Gram row (V^T v_{k-1})_j over this CTA's rows
             rows_times_matrix(f.V, f.ldv, r0, r1, k, [&](int r) { return f.V[(size_t)r * f.ldv + (k - 1)]; },
                               pA + N, sm);
@@ -1154,7 +1471,48 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
 
         const bool small_k = k <= f.redundant_max;  // k-vectors reduced by every CTA
         const int nk0 = (gs && k > 0 && small_k) ? k : 0;
-        gather_reduce(f, sm, G, 1, 0, 0, f.partA, f.LA, nc1 + nk0, slice_then_k, rb);
+        gather_reduce(f, sm, G, cand ? 2 : 1, 0, 1, f.partA, f.LA, nc1 + nk0, slice_then_k, rb);
+        if (cand) {
+            // Rayleigh quotients ||R^T v||^2 / ||v||^2 of both starts; the learned one
+            // replaces the paper's when its quotient is larger (and R(k) is nonzero)
+            const ff va2 = sm.sff[0], vb2 = sm.sff[1];
+            float* sbv = ka + f.ldk;  // this CTA's slice of s_b
+            gather_reduce(f, sm, G, 0, 0, 0, f.pC, N, nc1, [&](int v) { return n0 + v; }, sbv);
+            ff qa = ff_zero(), qb = ff_zero();
+            for (int v = tid; v < nc1; v += T) {
+                qa = ff_add(qa, ff_sqr(sv[v]));
+                qb = ff_add(qb, ff_sqr(sbv[v]));
+            }
+            qa = block_sum_ff(qa, sm);
+            qb = block_sum_ff(qb, sm);
+            if (tid == 0) {
+                float* wp = f.wsPart + (size_t)g * 32;
+                wp[24] = qa.hi;
+                wp[25] = qa.lo;
+                wp[26] = qb.hi;
+                wp[27] = qb.lo;
+            }
+            GS_SYNC();
+            if (tid == 0) {
+                double Sa = 0.0, Sb = 0.0;
+                for (int g2 = 0; g2 < G; ++g2) {
+                    const float* wq = f.wsPart + (size_t)g2 * 32;
+                    Sa += (double)ldcg(wq + 24) + (double)ldcg(wq + 25);
+                    Sb += (double)ldcg(wq + 26) + (double)ldcg(wq + 27);
+                }
+                const double na = ff_to_double(va2), nb = ff_to_double(vb2);
+                sm.sel = (na > 0.0 && nb > 0.0 && Sb / nb > Sa / na) ? 1 : 0;
+            }
+            __syncthreads();
+            const int use = sm.sel;
+            if (use)
+                for (int v = tid; v < nc1; v += T) sv[v] = sbv[v];
+            if (tid == 0) sm.sff[0] = use ? vb2 : va2;
+            if (g == 0 && tid == 0 && f.ws_choice) f.ws_choice[k] = use;
+            __syncthreads();
+        } else if (wsk && g == 0 && tid == 0 && f.ws_choice) {
+            f.ws_choice[k] = 0;
+        }
         if (sm.sff[0].hi == 0.f && sm.sff[0].lo == 0.f) {
             // Zero start column: restart from the residual column of largest
             // norm (lowest index on ties); every column zero => rank exhausted.

@@ -54,7 +54,34 @@ gspca_status check_fit_args(gspca_t h, const void* X, gspca_layout layout, long 
         if (opts->iters_lock)
             for (int k = 0; k < K; ++k)
                 if (opts->iters_lock[k] < 1) return GSPCA_ERR_INVALID_ARG;
+        if (opts->warm) {
+            const gspca_warm_start* w = opts->warm;
+            if (!w->net || !w->G || w->G_rows < M) return GSPCA_ERR_INVALID_ARG;
+            if (algo != GSPCA_GS) return GSPCA_ERR_NOT_SUPPORTED;
+        }
     }
+    return GSPCA_OK;
+}
+
+// Give the handle's workspace the buffers of the learned warm start (once).
+gspca_status ensure_warm(gspca_t h) {
+    if (h->ws.wsF) return GSPCA_OK;
+    WsDims dims{(h->max_M + 3) / 4 * 4, (int)h->max_N, h->max_K, h->num_sms, true};
+    const Workspace probe = carve(nullptr, dims);
+    void* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, probe.bytes);
+    if (e != cudaSuccess) {
+        cuda_ok(e);
+        return e == cudaErrorMemoryAllocation ? GSPCA_ERR_OOM : GSPCA_ERR_CUDA;
+    }
+    if (!cuda_ok(cudaMemset(base, 0, probe.bytes))) {
+        cudaFree(base);
+        return GSPCA_ERR_CUDA;
+    }
+    GS_CUDA(cudaDeviceSynchronize());  // no work of an earlier call may still use the old workspace
+    GS_CUDA(cudaFree(h->ws_base));
+    h->ws_base = base;
+    h->ws = carve(base, dims);
     return GSPCA_OK;
 }
 
@@ -67,6 +94,11 @@ gspca_status enqueue_fit(gspca_t h, cudaStream_t s, const float* X, gspca_layout
     const int np = (M + 3) / 4;
     const int nxpart = ((N + 31) / 32) * ((np + 31) / 32);
     if (nxpart > h->ws.xcap) return GSPCA_ERR_NOT_SUPPORTED;
+    const gspca_warm_start* warm = opts ? opts->warm : nullptr;
+    if (warm) {
+        const gspca_status ws = ensure_warm(h);
+        if (ws != GSPCA_OK) return ws;
+    }
     Plan plan{};
     GS_CUDA(plan_fit(h->device, h->num_sms, h->ws.G, M, N, K, cell_bytes(h->dtype), opts, &plan));
     const int* lock_dev = nullptr;
@@ -76,6 +108,16 @@ gspca_status enqueue_fit(gspca_t h, cudaStream_t s, const float* X, gspca_layout
     }
     FitArgs a = make_args(h->ws, plan, M, N, K, tol, max_iter, algo, lock_dev, timeout, nxpart);
     if (opts && opts->test_stall) a.stall_word = h->ws.abort + 2;  // a word nothing sets
+    if (warm) {
+        a.ws_net = warm->net;
+        a.ws_G = warm->G;
+        a.wsF = h->ws.wsF;
+        a.wsP0 = h->ws.wsP0;
+        a.pC = h->ws.pC;
+        a.wsPart = h->ws.wsPart;
+        a.wsInit = h->ws.wsInit;
+        a.ws_choice = warm->choice;
+    }
 #ifdef GSPCA_PHASE_TIMING
     if (!g_timing_dev) cudaMalloc(&g_timing_dev, 16 * sizeof(unsigned long long));
     cudaMemsetAsync(g_timing_dev, 0, 16 * sizeof(unsigned long long), s);
@@ -257,6 +299,7 @@ gspca_status gspca_destroy(gspca_t h) {
     gspca_status st = GSPCA_OK;
     if (h->stage && !cuda_ok(cudaFree(h->stage))) st = GSPCA_ERR_CUDA;
     if (h->ws_base && !cuda_ok(cudaFree(h->ws_base))) st = GSPCA_ERR_CUDA;
+    if (h->ws_train && !cuda_ok(cudaFree(h->ws_train))) st = GSPCA_ERR_CUDA;
     if (h->h_info && !cuda_ok(cudaFreeHost(h->h_info))) st = GSPCA_ERR_CUDA;
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);

@@ -66,4 +66,6 @@ struct gspca_handle {
     int* siters = nullptr;
     gspca_info last{};
     gspca::BatchState batch;
+    void* ws_train = nullptr;       // scratch of gspca_ws_train_step (grown on demand)
+    size_t ws_train_bytes = 0;
 };

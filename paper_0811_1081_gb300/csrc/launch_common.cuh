@@ -24,6 +24,10 @@ struct Plan {
     size_t dyn;
 };
 
+// Shared memory after the ring: the CTA's slice of the pass result, two
+// k-vectors, and the slice of the learned start's second pass result.
+inline size_t vec_bytes(int ldk, int max_slice) { return sizeof(float) * (2 * (size_t)ldk + 2 * (size_t)max_slice); }
+
 // Bytes of one cell of R (4 rows x 1 column) for a storage type.
 inline int cell_bytes(gspca_dtype dt) { return dt == GSPCA_BF16 ? 8 : 16; }
 
@@ -80,7 +84,7 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
     p->G = G;
     p->ldk = ws_ld(K);
     p->max_slice = (N + G - 1) / G + 1;
-    const size_t vec = sizeof(float) * (2 * (size_t)p->ldk + p->max_slice);
+    const size_t vec = vec_bytes(p->ldk, p->max_slice);
     int optin = 0;
     cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (e != cudaSuccess) return e;
@@ -169,7 +173,7 @@ inline FitArgs make_args(const Workspace& w, const Plan& p, int M, int N, int K,
     a.timing = nullptr;
     a.tma_stages = p.S;
     a.dot_groups = p.groups;
-    a.ring_bytes = (int)(p.dyn - sizeof(float) * (2 * (size_t)p.ldk + p.max_slice));
+    a.ring_bytes = (int)(p.dyn - vec_bytes(p.ldk, p.max_slice));
     a.ldk = p.ldk;
     a.max_slice = p.max_slice;
     a.redundant_max = kRedundantMax;

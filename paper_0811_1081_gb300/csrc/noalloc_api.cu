@@ -56,6 +56,7 @@ extern "C" gspca_status gspca_fit_noalloc(void* stream, const float* X, gspca_la
         (layout != GSPCA_COL_MAJOR && layout != GSPCA_ROW_MAJOR))
         return GSPCA_ERR_INVALID_ARG;
     if (opts) {
+        if (opts->warm) return GSPCA_ERR_NOT_SUPPORTED;  // its buffers are not part of the fixed scratch
         if (opts->center < 0 || opts->center > 2 || opts->grid_ctas < 0 || opts->timeout_s < 0 ||
             opts->test_stall < 0 || opts->test_stall > 1)
             return GSPCA_ERR_INVALID_ARG;

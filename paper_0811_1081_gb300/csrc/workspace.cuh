@@ -16,6 +16,7 @@ struct WsDims {
     long Mp;   // rows rounded up to a multiple of 4
     int N, K;
     int G;     // CTAs the partial buffers hold
+    bool warm = false;  // with the buffers of the learned warm start
 };
 
 // Leading dimension of the k-column factors: a power of two up to 128 (the
@@ -31,6 +32,7 @@ inline int ws_xcap(long Mp, int N) { return (int)(((N + 31) / 32) * ((Mp / 4 + 3
 
 struct Workspace {
     float *R, *V, *U, *W, *vraw, *vcorr, *ut, *upre, *partA, *partB;
+    float *wsF, *wsP0, *pC, *wsPart, *wsInit;  // learned warm start (null unless WsDims::warm)
     float2* spart;
     double *red, *lam, *xpart, *cmean, *rmean;
     int *iters, *info, *abort, *lock;
@@ -76,6 +78,13 @@ inline Workspace carve(void* base, const WsDims& d) {
     w.abort = (int*)take(sizeof(int) * 4);
     w.lock = (int*)take(sizeof(int) * (size_t)d.K);
     w.flags = (unsigned*)take(sizeof(unsigned) * 32);
+    if (d.warm) {
+        w.wsF = (float*)take(sizeof(float) * 17 * (size_t)d.N);
+        w.wsP0 = (float*)take(sizeof(float) * (size_t)d.N);
+        w.pC = (float*)take(sizeof(float) * (size_t)d.G * d.N);
+        w.wsPart = (float*)take(sizeof(float) * 32 * (size_t)d.G);
+        w.wsInit = (float*)take(sizeof(float) * 17 * (size_t)d.G * d.N);
+    }
     w.bytes = off;
     return w;
 }
