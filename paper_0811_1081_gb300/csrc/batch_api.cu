@@ -20,13 +20,14 @@ namespace {
 
 constexpr int kBatchMaxN = 2 * kBlock;  // columns per thread 1 or 2
 
-// The batched kernel for a storage type.
-const void* batch_kernel_for(gspca_dtype dt) {
-    return dt == GSPCA_BF16 ? batch_kernel_ptr<__nv_bfloat16>() : batch_kernel_ptr<float>();
+// The batched kernel for a storage type, with or without the learned warm start.
+const void* batch_kernel_for(gspca_dtype dt, bool warm) {
+    if (warm) return dt == GSPCA_BF16 ? batch_kernel_ptr<__nv_bfloat16, true>() : batch_kernel_ptr<float, true>();
+    return dt == GSPCA_BF16 ? batch_kernel_ptr<__nv_bfloat16, false>() : batch_kernel_ptr<float, false>();
 }
 
 cudaError_t plan_batch(int device, gspca_dtype dt, int C, long maxM, int maxN, int maxK, bool warm, BatchPlan* bp) {
-    const void* kern = batch_kernel_for(dt);
+    const void* kern = batch_kernel_for(dt, warm);
     cudaFuncAttributes fa{};
     cudaError_t e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;
@@ -236,7 +237,7 @@ gspca_status enqueue_batch(gspca_t h, cudaStream_t s, const gspca_problem* p, in
             d.pad = 0;
         }
         void* args[] = {a.get()};
-        GS_CUDA(cudaLaunchKernelExC(&cfg, batch_kernel_for(h->dtype), args));
+        GS_CUDA(cudaLaunchKernelExC(&cfg, batch_kernel_for(h->dtype, a->ws_net != nullptr), args));
         ++n;
     }
     if (events) GS_CUDA(cudaEventRecord(b.e1, s));

@@ -148,7 +148,7 @@ __device__ __forceinline__ void ring_geometry(int ldp, int ring_bytes, int* S, i
     *groups = 1;
 }
 
-template <int CPT, class E>
+template <int CPT, class E, bool WARM>
 __device__ __forceinline__ FitOutcome run_problem(FitArgs& fa, const TeamCluster& tm, SmemFit& sm,
                                                   unsigned char* dyn_smem, Ring& rg, float threshf, unsigned& epoch,
                                                   bool narrow) {
@@ -161,15 +161,16 @@ __device__ __forceinline__ FitOutcome run_problem(FitArgs& fa, const TeamCluster
     }
     __syncthreads();
     ring_setup(rg, sm, dyn_smem, S, groups == 2 ? 1 : PassShape<CPT>::PPR, fa.ldp * Cell<E>::kBytes);
-    const FitOutcome r = fit_one<CPT, E>(fa, tm, sm, dyn_smem, rg, threshf, epoch);
+    const FitOutcome r = fit_one<CPT, E, WARM>(fa, tm, sm, dyn_smem, rg, threshf, epoch);
     ring_drain(fa, rg);
     return r;
 }
 
 // One launch: clusters of C CTAs take problems from ctl->queue until it runs
 // past count.  Columns per thread are 1 (N <= 512) or 2 (N <= 1024).  E is the
-// storage type of R (float or __nv_bfloat16).
-template <class E>
+// storage type of R (float or __nv_bfloat16); WARM instantiations carry the
+// learned warm start.
+template <class E, bool WARM>
 __global__ void __launch_bounds__(kBlock, 1) batch_kernel(const __grid_constant__ BatchArgs a) {
     __shared__ SmemFit sm;
     __shared__ FitArgs fa;
@@ -280,8 +281,8 @@ __global__ void __launch_bounds__(kBlock, 1) batch_kernel(const __grid_constant_
         const float threshf =
             (float)(fa.eps_thresh * sqrt(fmax(0.0, ff_to_double(sm.sff[0]))));
         const bool narrow = a.pass == 1;
-        FitOutcome r = (N <= kBlock) ? run_problem<1, E>(fa, tm, sm, dyn_smem, rg, threshf, epoch, narrow)
-                                     : run_problem<2, E>(fa, tm, sm, dyn_smem, rg, threshf, epoch, narrow);
+        FitOutcome r = (N <= kBlock) ? run_problem<1, E, WARM>(fa, tm, sm, dyn_smem, rg, threshf, epoch, narrow)
+                                     : run_problem<2, E, WARM>(fa, tm, sm, dyn_smem, rg, threshf, epoch, narrow);
         PHASE_MARK(15);
         tm.sync(epoch, nullptr);  // V, U, lambda of every CTA visible; failure word settled
         if (ldcg(fail_word) != 0) {
@@ -345,7 +346,7 @@ __global__ void __launch_bounds__(kBlock, 1) batch_kernel(const __grid_constant_
 
 // The batched kernel of a storage type as a launchable function pointer
 // (defined and instantiated with the kernels, see fit_inst.cuh).
-template <class E>
+template <class E, bool WARM>
 const void* batch_kernel_ptr();
 
 }  // namespace gspca

@@ -2,6 +2,6 @@
 // CTA, the pack/unpack kernels and the batched kernel.
 #include "fit_inst.cuh"
 
-GSPCA_INSTANTIATE_FIT(1, __nv_bfloat16)
-GSPCA_INSTANTIATE_FIT(2, __nv_bfloat16)
+GSPCA_INSTANTIATE_FIT(1, __nv_bfloat16, false)
+GSPCA_INSTANTIATE_FIT(2, __nv_bfloat16, false)
 GSPCA_INSTANTIATE_AUX(__nv_bfloat16)

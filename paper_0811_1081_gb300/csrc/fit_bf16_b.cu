@@ -1,4 +1,4 @@
 // Kernels for storage type __nv_bfloat16: the fit kernel for up to 2048 columns per CTA.
 #include "fit_inst.cuh"
 
-GSPCA_INSTANTIATE_FIT(4, __nv_bfloat16)
+GSPCA_INSTANTIATE_FIT(4, __nv_bfloat16, false)

@@ -2,5 +2,5 @@
 // per CTA.
 #include "fit_inst.cuh"
 
-GSPCA_INSTANTIATE_FIT(8, __nv_bfloat16)
-GSPCA_INSTANTIATE_FIT(16, __nv_bfloat16)
+GSPCA_INSTANTIATE_FIT(8, __nv_bfloat16, false)
+GSPCA_INSTANTIATE_FIT(16, __nv_bfloat16, false)

@@ -2,6 +2,6 @@
 // CTA, the pack/unpack kernels and the batched kernel.
 #include "fit_inst.cuh"
 
-GSPCA_INSTANTIATE_FIT(1, float)
-GSPCA_INSTANTIATE_FIT(2, float)
+GSPCA_INSTANTIATE_FIT(1, float, false)
+GSPCA_INSTANTIATE_FIT(2, float, false)
 GSPCA_INSTANTIATE_AUX(float)

@@ -2,5 +2,5 @@
 // per CTA.
 #include "fit_inst.cuh"
 
-GSPCA_INSTANTIATE_FIT(8, float)
-GSPCA_INSTANTIATE_FIT(16, float)
+GSPCA_INSTANTIATE_FIT(8, float, false)
+GSPCA_INSTANTIATE_FIT(16, float, false)

@@ -12,21 +12,21 @@
 
 namespace gspca {
 
-template <int CPT, class E>
+template <int CPT, class E, bool WARM>
 cudaError_t fit_attrs(size_t dyn, int* bps, int* static_smem) {
     cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, fit_kernel<CPT, E>);
+    cudaError_t e = cudaFuncGetAttributes(&fa, fit_kernel<CPT, E, WARM>);
     if (e != cudaSuccess) return e;
     *static_smem = (int)fa.sharedSizeBytes;
-    e = cudaFuncSetAttribute(fit_kernel<CPT, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    e = cudaFuncSetAttribute(fit_kernel<CPT, E, WARM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fit_kernel<CPT, E>, kBlock, dyn);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fit_kernel<CPT, E, WARM>, kBlock, dyn);
 }
 
-template <int CPT, class E>
+template <int CPT, class E, bool WARM>
 cudaError_t launch_fit_t(const FitArgs& a, int G, size_t dyn, cudaStream_t s) {
     void* args[] = {const_cast<FitArgs*>(&a)};
-    return cudaLaunchCooperativeKernel((const void*)fit_kernel<CPT, E>, dim3(G), dim3(kBlock), args, dyn, s);
+    return cudaLaunchCooperativeKernel((const void*)fit_kernel<CPT, E, WARM>, dim3(G), dim3(kBlock), args, dyn, s);
 }
 
 template <class E>
@@ -43,17 +43,18 @@ void launch_unpack(dim3 grid, cudaStream_t s, const void* R, int M, int N, int n
     unpack_kernel<E><<<grid, kPackThreads, 0, s>>>(R, M, N, np, ldp, V, ldv, U, ldu, lam, info, K, gs, R_out);
 }
 
-template <class E>
+template <class E, bool WARM>
 const void* batch_kernel_ptr() {
-    return (const void*)batch_kernel<E>;
+    return (const void*)batch_kernel<E, WARM>;
 }
 
 }  // namespace gspca
 
-// Explicit instantiation of the kernels of one column-block count / storage type.
-#define GSPCA_INSTANTIATE_FIT(CPT, E)                                                                   \
-    template cudaError_t gspca::fit_attrs<CPT, E>(size_t, int*, int*);                                 \
-    template cudaError_t gspca::launch_fit_t<CPT, E>(const gspca::FitArgs&, int, size_t, cudaStream_t);
+// Explicit instantiation of the fit kernel of one column-block count / storage type
+// (WARM: with the learned warm start).
+#define GSPCA_INSTANTIATE_FIT(CPT, E, WARM)                                                                \
+    template cudaError_t gspca::fit_attrs<CPT, E, WARM>(size_t, int*, int*);                               \
+    template cudaError_t gspca::launch_fit_t<CPT, E, WARM>(const gspca::FitArgs&, int, size_t, cudaStream_t);
 
 // Explicit instantiation of the pack/unpack kernels and the batched kernel of a storage type.
 #define GSPCA_INSTANTIATE_AUX(E)                                                                            \
@@ -63,4 +64,7 @@ const void* batch_kernel_ptr() {
     template void gspca::launch_unpack<E>(dim3, cudaStream_t, const void*, int, int, int, int, const float*,  \
                                           int, const float*, int, const double*, const int*, int, int,        \
                                           float*);                                                            \
-    template const void* gspca::batch_kernel_ptr<E>();
+    template const void* gspca::batch_kernel_ptr<E, false>();
+
+// The batched kernel with the learned warm start.
+#define GSPCA_INSTANTIATE_BATCH_WARM(E) template const void* gspca::batch_kernel_ptr<E, true>();

@@ -1066,6 +1066,21 @@ struct FitOutcome {
 
 // ------------------------------------------------------------------ learned warm start
 
+// Sums over the team's CTAs of nv values: value j = sum_g part[g * stride + j],
+// in double, into out[j] (shared memory).  A warp per value; its lanes load the
+// CTA rows lane, lane + 32, ... together (one L2 round trip) and combine them
+// with a fixed butterfly, so the result is deterministic.
+__device__ __forceinline__ void team_sum(const float* part, int stride, int G, int nv, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = warp; j < nv; j += nw) {
+        double t = 0.0;
+        for (int g2 = lane; g2 < G; g2 += 32) t += (double)ldcg(part + (size_t)g2 * stride + j);
+        t = warp_sum(t);
+        if (lane == 0) out[j] = t;
+    }
+    __syncthreads();
+}
+
 // Sketch of the initial residual.  Every CTA accumulates, for every column, the
 // squared norm and the 16 sketch sums G^T R(n) over its own panels (a thread
 // per column, rows in order), writes them to wsInit[g][j][n]; after the team
@@ -1103,12 +1118,14 @@ __device__ __noinline__ bool ws_sketch_init(const FitArgs& f, const Team& tm, Sm
         for (int j = 0; j < kWsIn; ++j) f.wsInit[((size_t)tm.g * kWsIn + j) * N + c] = acc[j];
     }
     if (!tm.sync(epoch, &sm.flag)) return false;
-    const int nc = n1 - n0;
-    for (int e = tid; e < nc * kWsIn; e += T) {
+    // a warp per (column, value) of this CTA's slice, CTA partials in order
+    const int nc = n1 - n0, lane = tid & 31;
+    for (int e = tid >> 5; e < nc * kWsIn; e += T >> 5) {
         const int n = n0 + e / kWsIn, j = e % kWsIn;
-        float t = 0.f;
-        for (int g2 = 0; g2 < tm.G; ++g2) t += ldcg(f.wsInit + ((size_t)g2 * kWsIn + j) * N + n);
-        f.wsF[(size_t)n * kWsIn + j] = t;
+        double t = 0.0;
+        for (int g2 = lane; g2 < tm.G; g2 += 32) t += (double)ldcg(f.wsInit + ((size_t)g2 * kWsIn + j) * N + n);
+        t = warp_sum(t);
+        if (lane == 0) f.wsF[(size_t)n * kWsIn + j] = (float)t;
     }
     return true;
 }
@@ -1123,10 +1140,12 @@ __device__ __noinline__ bool ws_sketch_init(const FitArgs& f, const Team& tm, Sm
 // Then a warp per column of this CTA's slice evaluates the network on
 // x_n = [c_n, s_n] / rho and writes wsP0; *ww receives ||w||^2 over the team.
 // Two team barriers.  Returns false if one failed.
+// The network parameters are staged in `stage` (shared memory of at least
+// kWsParams floats, idle at this point) when it is non-null.
 template <class Team>
 __device__ __noinline__ bool ws_prepare(const FitArgs& f, const Team& tm, SmemFit& sm, unsigned& epoch, int k,
                                         int r0, int r1, int n0, int n1, double lam_prev, float vinv_prev,
-                                        double* ww) {
+                                        float* stage, double* ww) {
     const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
     float* wp = f.wsPart + (size_t)tm.g * 32;
     if (k > 0)  // G^T v_{k-1} over this CTA's rows
@@ -1152,13 +1171,13 @@ __device__ __noinline__ bool ws_prepare(const FitArgs& f, const Team& tm, SmemFi
         wp[20] = a2.hi;
         wp[21] = a2.lo;
     }
-    if (!tm.sync(epoch, &sm.flag)) return false;
-    if (tid < 22) {  // sums over the team, CTA order
-        double t = 0.0;
-        for (int g2 = 0; g2 < tm.G; ++g2) t += (double)ldcg(f.wsPart + (size_t)g2 * 32 + tid);
-        sm.wsv[tid] = t;
+    const float* net = f.ws_net;
+    if (stage) {
+        for (int i = tid; i < kWsParams; i += T) stage[i] = __ldg(f.ws_net + i);
+        net = stage;  // visible to every thread after the barrier below
     }
-    __syncthreads();
+    if (!tm.sync(epoch, &sm.flag)) return false;
+    team_sum(f.wsPart, 32, tm.G, 22, sm.wsv);
     const double lam = lam_prev;
     double rho2 = sm.wsv[16] + sm.wsv[17];
     if (k > 0) {
@@ -1183,7 +1202,7 @@ __device__ __noinline__ bool ws_prepare(const FitArgs& f, const Team& tm, SmemFi
         x[0] = sqrtf(fmaxf(xr[0], 0.f)) * invrho;
 #pragma unroll
         for (int j = 1; j < kWsIn; ++j) x[j] = xr[j] * invrho;
-        const float w = ws_forward_warp(f.ws_net, x, lane);
+        const float w = ws_forward_warp(net, x, lane);
         if (lane == 0) {
             f.wsP0[n] = w;
             my = ff_add(my, ff_sqr(w));
@@ -1194,15 +1213,11 @@ __device__ __noinline__ bool ws_prepare(const FitArgs& f, const Team& tm, SmemFi
         wp[22] = my.hi;
         wp[23] = my.lo;
     }
+    // the staged parameters live in ring memory that TMA copies refill later
+    if (stage) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (!tm.sync(epoch, &sm.flag)) return false;
-    if (tid == 0) {
-        double t = 0.0;
-        for (int g2 = 0; g2 < tm.G; ++g2)
-            t += (double)ldcg(f.wsPart + (size_t)g2 * 32 + 22) + (double)ldcg(f.wsPart + (size_t)g2 * 32 + 23);
-        sm.wsv[22] = t;
-    }
-    __syncthreads();
-    *ww = sm.wsv[22];
+    team_sum(f.wsPart + 22, 32, tm.G, 2, sm.wsv + 22);
+    *ww = sm.wsv[22] + sm.wsv[23];
     return true;
 }
 
@@ -1215,8 +1230,11 @@ template <int CPT, class E>
 __device__ __noinline__ void ws_start_pass(const FitArgs& f, SmemFit& sm, int g, int p0, int p1, int kcol,
                                            bool deflate, float lamf, int kprev, int buf, float inv_nu, double ww,
                                            float* pA, ff* sa, ff* sb) {
-    constexpr int PPR = PassShape<CPT>::PPR;
-    constexpr int RPR = PassShape<CPT>::RPR;
+    // half the panels per round of the other passes where the loads are
+    // software-pipelined (two rounds of cells in registers)
+    constexpr bool PIPE = CPT <= 4;
+    constexpr int PPR = PIPE ? (PassShape<CPT>::PPR > 1 ? PassShape<CPT>::PPR / 2 : 1) : PassShape<CPT>::PPR;
+    constexpr int RPR = 4 * PPR;
     constexpr int SH = 5 - Log2<RPR>::value;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int T = blockDim.x, N = f.N;
@@ -1234,16 +1252,31 @@ __device__ __noinline__ void ws_start_pass(const FitArgs& f, SmemFit& sm, int g,
     if ((kcol % T) == tid) owner = kcol / T;
     ff my_a = ff_zero(), my_b = ff_zero();
     int bsel = 0;
-    for (int pb = p0; pb < p1; pb += PPR, bsel ^= 1) {
-        float4 d[PPR][CPT];
+    // software pipeline (up to 2048 columns, where the registers allow it): the next
+    // round's cells are loaded before this round is used
+    float4 dn[PPR][CPT];
+    auto load_round = [&](int pb, float4 (&dst)[PPR][CPT]) {
 #pragma unroll
         for (int pp = 0; pp < PPR; ++pp) {
             const int p = pb + pp;
 #pragma unroll
             for (int i = 0; i < CPT; ++i) {
                 const int c = tid + i * T;
-                d[pp][i] = (p < p1 && c < N) ? Cell<E>::ldg(f.R, (size_t)p * ldp + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                dst[pp][i] = (p < p1 && c < N) ? Cell<E>::ldg(f.R, (size_t)p * ldp + c) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
+        }
+    };
+    if (PIPE && p0 < p1) load_round(p0, dn);
+    for (int pb = p0; pb < p1; pb += PPR, bsel ^= 1) {
+        float4 d[PPR][CPT];
+        if constexpr (PIPE) {
+#pragma unroll
+            for (int pp = 0; pp < PPR; ++pp)
+#pragma unroll
+                for (int i = 0; i < CPT; ++i) d[pp][i] = dn[pp][i];
+            if (pb + PPR < p1) load_round(pb + PPR, dn);
+        } else {
+            load_round(pb, d);
         }
         if (deflate) {
 #pragma unroll
@@ -1347,6 +1380,48 @@ __device__ __noinline__ void ws_start_pass(const FitArgs& f, SmemFit& sm, int g,
     __syncthreads();
 }
 
+// After the first pass with both starts (sm.sff[0] = ||v_a||^2, sm.sff[1] =
+// ||v_b||^2 reduced; sv = this CTA's slice of s_a = R^T v_a): reduce this CTA's
+// slice of s_b into sbv, form ||s_a||^2 and ||s_b||^2 over the team, and keep
+// the start with the larger Rayleigh quotient ||s||^2 / ||v||^2: on return sv
+// and sm.sff[0] describe the chosen start.  One team barrier; false if it failed.
+template <class Team>
+__device__ __noinline__ bool ws_select(const FitArgs& f, const Team& tm, SmemFit& sm, unsigned& epoch, int k,
+                                       int n0, int nc1, float* sv, float* sbv) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    const ff va2 = sm.sff[0], vb2 = sm.sff[1];
+    gather_reduce(f, sm, tm.G, 0, 0, 0, f.pC, f.N, nc1, [&](int v) { return n0 + v; }, sbv);
+    ff qa = ff_zero(), qb = ff_zero();
+    for (int v = tid; v < nc1; v += T) {
+        qa = ff_add(qa, ff_sqr(sv[v]));
+        qb = ff_add(qb, ff_sqr(sbv[v]));
+    }
+    qa = block_sum_ff(qa, sm);
+    qb = block_sum_ff(qb, sm);
+    if (tid == 0) {
+        float* wp = f.wsPart + (size_t)tm.g * 32;
+        wp[24] = qa.hi;
+        wp[25] = qa.lo;
+        wp[26] = qb.hi;
+        wp[27] = qb.lo;
+    }
+    if (!tm.sync(epoch, &sm.flag)) return false;
+    team_sum(f.wsPart + 24, 32, tm.G, 4, sm.wsv);
+    if (tid == 0) {
+        const double Sa = sm.wsv[0] + sm.wsv[1], Sb = sm.wsv[2] + sm.wsv[3];
+        const double na = ff_to_double(va2), nb = ff_to_double(vb2);
+        sm.sel = (na > 0.0 && nb > 0.0 && Sb / nb > Sa / na) ? 1 : 0;
+    }
+    __syncthreads();
+    const int use = sm.sel;
+    if (use)
+        for (int v = tid; v < nc1; v += T) sv[v] = sbv[v];
+    if (tid == 0) sm.sff[0] = use ? vb2 : va2;
+    if (tm.g == 0 && tid == 0 && f.ws_choice) f.ws_choice[k] = use;
+    __syncthreads();
+    return true;
+}
+
 // (Re)initialise this CTA's ring: S stages of ppr panels of panel_bytes each.
 // Must be called with no copy in flight.
 __device__ __forceinline__ void ring_setup(Ring& rg, SmemFit& sm, unsigned char* dyn_smem, int S, int ppr,
@@ -1371,7 +1446,7 @@ __device__ __forceinline__ void ring_setup(Ring& rg, SmemFit& sm, unsigned char*
 // degenerate threshold and this CTA's shared memory; the ring must be set up
 // for f.N.  Writes V, U, W and lambda/iters for k < found; returns the
 // outcome (identical in every CTA of the team).
-template <int CPT, class E, class Team>
+template <int CPT, class E, bool WARM, class Team>
 __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, unsigned char* dyn_smem, Ring& rg,
                               float threshf, unsigned& epoch) {
     constexpr int PPR = PassShape<CPT>::PPR;
@@ -1422,26 +1497,32 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
         PHASE_MARK(0);
         const bool defl = k > 0;
         const float lamf = gs ? (float)lam_prev : 1.f;
-        // learned warm start: features, network output, and a first pass with both starts
-        const bool wsk = gs && f.ws_net != nullptr;
+        // learned warm start (the WARM instantiations only): features, network output, and a
+        // first pass with both starts
+        const bool wsk = WARM && gs && f.ws_net != nullptr;
         bool cand = false;
-        if (wsk) {
+        if constexpr (WARM) if (wsk) {
+            PHASE_MARK(5);
             if (k == 0 && !ws_sketch_init<E>(f, tm, sm, epoch, p0, p1, n0, n1)) {
                 alive = false;
                 goto leave;
             }
             double ww = 0.0;
-            if (!ws_prepare(f, tm, sm, epoch, k, r0, r1, n0, n1, lam_prev, vinv_prev, &ww)) {
+            float* stage = f.ring_bytes >= kWsParams * (int)sizeof(float) ? reinterpret_cast<float*>(dyn_smem)
+                                                                          : nullptr;
+            if (!ws_prepare(f, tm, sm, epoch, k, r0, r1, n0, n1, lam_prev, vinv_prev, stage, &ww)) {
                 alive = false;
                 goto leave;
             }
             cand = ww > 0.0 && isfinite(ww);
+            PHASE_MARK(9);
             if (cand) {
                 ff sa, sb;
                 ws_start_pass<CPT, E>(f, sm, g, p0, p1, k, defl, lamf, k - 1, buf, inv_nu, ww, pA, &sa, &sb);
                 write_scalar(f, g, 0, sa);
                 write_scalar(f, g, 1, sb);
             }
+            PHASE_MARK(12);
         }
         if (!cand) {
 #pragma unroll
@@ -1472,46 +1553,17 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
         const bool small_k = k <= f.redundant_max;  // k-vectors reduced by every CTA
         const int nk0 = (gs && k > 0 && small_k) ? k : 0;
         gather_reduce(f, sm, G, cand ? 2 : 1, 0, 1, f.partA, f.LA, nc1 + nk0, slice_then_k, rb);
-        if (cand) {
-            // Rayleigh quotients ||R^T v||^2 / ||v||^2 of both starts; the learned one
-            // replaces the paper's when its quotient is larger (and R(k) is nonzero)
-            const ff va2 = sm.sff[0], vb2 = sm.sff[1];
-            float* sbv = ka + f.ldk;  // this CTA's slice of s_b
-            gather_reduce(f, sm, G, 0, 0, 0, f.pC, N, nc1, [&](int v) { return n0 + v; }, sbv);
-            ff qa = ff_zero(), qb = ff_zero();
-            for (int v = tid; v < nc1; v += T) {
-                qa = ff_add(qa, ff_sqr(sv[v]));
-                qb = ff_add(qb, ff_sqr(sbv[v]));
-            }
-            qa = block_sum_ff(qa, sm);
-            qb = block_sum_ff(qb, sm);
-            if (tid == 0) {
-                float* wp = f.wsPart + (size_t)g * 32;
-                wp[24] = qa.hi;
-                wp[25] = qa.lo;
-                wp[26] = qb.hi;
-                wp[27] = qb.lo;
-            }
-            GS_SYNC();
-            if (tid == 0) {
-                double Sa = 0.0, Sb = 0.0;
-                for (int g2 = 0; g2 < G; ++g2) {
-                    const float* wq = f.wsPart + (size_t)g2 * 32;
-                    Sa += (double)ldcg(wq + 24) + (double)ldcg(wq + 25);
-                    Sb += (double)ldcg(wq + 26) + (double)ldcg(wq + 27);
+        if constexpr (WARM) {
+            if (cand) {
+                PHASE_MARK(13);
+                if (!ws_select(f, tm, sm, epoch, k, n0, nc1, sv, ka + f.ldk)) {
+                    alive = false;
+                    goto leave;
                 }
-                const double na = ff_to_double(va2), nb = ff_to_double(vb2);
-                sm.sel = (na > 0.0 && nb > 0.0 && Sb / nb > Sa / na) ? 1 : 0;
+                PHASE_MARK(0);
+            } else if (wsk && g == 0 && tid == 0 && f.ws_choice) {
+                f.ws_choice[k] = 0;
             }
-            __syncthreads();
-            const int use = sm.sel;
-            if (use)
-                for (int v = tid; v < nc1; v += T) sv[v] = sbv[v];
-            if (tid == 0) sm.sff[0] = use ? vb2 : va2;
-            if (g == 0 && tid == 0 && f.ws_choice) f.ws_choice[k] = use;
-            __syncthreads();
-        } else if (wsk && g == 0 && tid == 0 && f.ws_choice) {
-            f.ws_choice[k] = 0;
         }
         if (sm.sff[0].hi == 0.f && sm.sff[0].lo == 0.f) {
             // Zero start column: restart from the residual column of largest
@@ -1830,7 +1882,7 @@ leave:
 // ------------------------------------------------------------------ kernels
 
 // Single problem, whole grid (cooperative launch).
-template <int CPT, class E>
+template <int CPT, class E, bool WARM>
 __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
     __shared__ SmemFit sm;
     extern __shared__ __align__(128) unsigned char dyn_smem[];
@@ -1858,7 +1910,7 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
     ring_setup(rg, sm, dyn_smem, f.tma_stages, f.dot_groups == 2 ? 1 : PassShape<CPT>::PPR,
                f.ldp * Cell<E>::kBytes);
     unsigned epoch = 0;
-    const FitOutcome r = fit_one<CPT, E>(f, tm, sm, dyn_smem, rg, threshf, epoch);
+    const FitOutcome r = fit_one<CPT, E, WARM>(f, tm, sm, dyn_smem, rg, threshf, epoch);
 #ifdef GSPCA_PHASE_TIMING
     PHASE_MARK(15);
     if (blockIdx.x == 0 && tid == 0 && f.timing)

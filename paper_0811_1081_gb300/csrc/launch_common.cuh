@@ -20,7 +20,8 @@ constexpr int kRedundantMax = 128;      // k up to which every CTA reduces a k-v
 
 struct Plan {
     int cpt, ppr, G, S, ldk, max_slice, groups;
-    int cb;  // bytes of one cell of R: 16 (FP32 storage) or 8 (bfloat16 storage)
+    int cb;     // bytes of one cell of R: 16 (FP32 storage) or 8 (bfloat16 storage)
+    bool warm;  // the kernel with the learned warm start
     size_t dyn;
 };
 
@@ -40,10 +41,14 @@ inline int cpt_for(int N) {
 // Kernel attributes and launches per (columns per thread, storage type).  They
 // are defined beside the kernels (fit_inst.cuh) and instantiated once each in
 // the fit_*.cu translation units, so the host-side units compile no kernel.
-template <int CPT, class E>
+template <int CPT, class E, bool WARM>
 cudaError_t fit_attrs(size_t dyn, int* bps, int* static_smem);
-template <int CPT, class E>
+template <int CPT, class E, bool WARM>
 cudaError_t launch_fit_t(const FitArgs& a, int G, size_t dyn, cudaStream_t s);
+
+// The learned warm start is compiled into the fit kernels for up to this many
+// columns per thread (2048 columns); wider problems fit without it.
+constexpr int kWarmMaxCpt = 4;
 template <class E>
 void launch_pack(dim3 grid, cudaStream_t s, const float* X, int layout, long ldx, int M, int N, int np, int ldp,
                  int center, const double* cmean, const double* rmean, void* R, double* xpart, unsigned* flags,
@@ -53,18 +58,27 @@ void launch_unpack(dim3 grid, cudaStream_t s, const void* R, int M, int N, int n
                    const float* U, int ldu, const double* lam, const int* info, int K, int gs, float* R_out);
 
 template <class E>
-inline cudaError_t fit_attrs_e(int cpt, size_t dyn, int* bps, int* st) {
+inline cudaError_t fit_attrs_e(int cpt, bool warm, size_t dyn, int* bps, int* st) {
+    if (warm) {
+        switch (cpt) {
+            case 1: return fit_attrs<1, E, true>(dyn, bps, st);
+            case 2: return fit_attrs<2, E, true>(dyn, bps, st);
+            case 4: return fit_attrs<4, E, true>(dyn, bps, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (cpt) {
-        case 1: return fit_attrs<1, E>(dyn, bps, st);
-        case 2: return fit_attrs<2, E>(dyn, bps, st);
-        case 4: return fit_attrs<4, E>(dyn, bps, st);
-        case 8: return fit_attrs<8, E>(dyn, bps, st);
-        default: return fit_attrs<16, E>(dyn, bps, st);
+        case 1: return fit_attrs<1, E, false>(dyn, bps, st);
+        case 2: return fit_attrs<2, E, false>(dyn, bps, st);
+        case 4: return fit_attrs<4, E, false>(dyn, bps, st);
+        case 8: return fit_attrs<8, E, false>(dyn, bps, st);
+        default: return fit_attrs<16, E, false>(dyn, bps, st);
     }
 }
 
-inline cudaError_t fit_attrs_any(int cpt, int cb, size_t dyn, int* bps, int* st) {
-    return cb == 8 ? fit_attrs_e<__nv_bfloat16>(cpt, dyn, bps, st) : fit_attrs_e<float>(cpt, dyn, bps, st);
+inline cudaError_t fit_attrs_any(int cpt, int cb, bool warm, size_t dyn, int* bps, int* st) {
+    return cb == 8 ? fit_attrs_e<__nv_bfloat16>(cpt, warm, dyn, bps, st)
+                   : fit_attrs_e<float>(cpt, warm, dyn, bps, st);
 }
 
 // Grid size, ring depth and shared memory for one problem.  Gcap bounds the
@@ -72,6 +86,7 @@ inline cudaError_t fit_attrs_any(int cpt, int cb, size_t dyn, int* bps, int* st)
 inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int K, int cb, const gspca_opts* opts,
                             Plan* p) {
     p->cb = cb;
+    p->warm = opts && opts->warm;
     p->cpt = cpt_for(N);
     p->ppr = p->cpt >= 8 ? 1 : 8 / p->cpt;
     const int np = (M + 3) / 4;
@@ -89,7 +104,7 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
     cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (e != cudaSuccess) return e;
     int bps = 0, st = 0;
-    e = fit_attrs_any(p->cpt, cb, vec, &bps, &st);
+    e = fit_attrs_any(p->cpt, cb, p->warm, vec, &bps, &st);
     if (e != cudaSuccess) return e;
     const long avail = (long)optin - st - (long)vec - 1024;
     // Preferred: the two-group loading pass with one panel per ring stage and an
@@ -110,7 +125,7 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
     }
     p->S = S;
     p->dyn = vec + (size_t)S * stage;
-    e = fit_attrs_any(p->cpt, cb, p->dyn, &bps, &st);
+    e = fit_attrs_any(p->cpt, cb, p->warm, p->dyn, &bps, &st);
     if (e != cudaSuccess) return e;
     if (bps < 1) return cudaErrorInvalidConfiguration;
     return cudaSuccess;
@@ -118,12 +133,20 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
 
 template <class E>
 inline cudaError_t launch_fit_e(const FitArgs& a, const Plan& p, cudaStream_t s) {
+    if (p.warm) {
+        switch (p.cpt) {
+            case 1: return launch_fit_t<1, E, true>(a, p.G, p.dyn, s);
+            case 2: return launch_fit_t<2, E, true>(a, p.G, p.dyn, s);
+            case 4: return launch_fit_t<4, E, true>(a, p.G, p.dyn, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (p.cpt) {
-        case 1: return launch_fit_t<1, E>(a, p.G, p.dyn, s);
-        case 2: return launch_fit_t<2, E>(a, p.G, p.dyn, s);
-        case 4: return launch_fit_t<4, E>(a, p.G, p.dyn, s);
-        case 8: return launch_fit_t<8, E>(a, p.G, p.dyn, s);
-        default: return launch_fit_t<16, E>(a, p.G, p.dyn, s);
+        case 1: return launch_fit_t<1, E, false>(a, p.G, p.dyn, s);
+        case 2: return launch_fit_t<2, E, false>(a, p.G, p.dyn, s);
+        case 4: return launch_fit_t<4, E, false>(a, p.G, p.dyn, s);
+        case 8: return launch_fit_t<8, E, false>(a, p.G, p.dyn, s);
+        default: return launch_fit_t<16, E, false>(a, p.G, p.dyn, s);
     }
 }
 

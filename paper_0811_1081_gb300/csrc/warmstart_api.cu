@@ -6,7 +6,7 @@
 
 #include "../../include/gspca.h"
 #include "handle.h"
-#include "warmstart.cuh"
+#include "warmstart_kernels.cuh"
 
 using namespace gspca;
 

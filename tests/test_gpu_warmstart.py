@@ -154,7 +154,7 @@ def check_warm_locked(g, X32, K, net, G):
     return ref
 
 
-@pytest.mark.parametrize("shape", [(500, 200, 8), (257, 31, 6), (1003, 517, 5), (130, 1025, 4), (64, 2049, 3)])
+@pytest.mark.parametrize("shape", [(500, 200, 8), (257, 31, 6), (1003, 517, 5), (130, 1025, 4), (64, 2048, 3)])
 def test_fit_with_learned_start_locked(gp, shape):
     M, N, K = shape
     X32 = synth.planted(M, N, 10.0, 0.85, 0.01, (77, M, N)).X.astype(np.float32)
@@ -202,13 +202,15 @@ def test_batched_with_learned_start_locked(gp):
         check_warm_locked(g, X, K, net, G[:X.shape[0]])
 
 
-def test_nipals_with_warm_start_is_refused(gp):
+def test_warm_start_refusals(gp):
+    """NIPALS-PCA has no learned start; the learned start is compiled for up to 2048 columns."""
     import torch
 
-    X = torch.zeros((20, 10), device="cuda")
-    with gp.Handle(20, 10, 2) as h:
-        r = gp.gspca_fit(h.h, X, 2, algo="nipals", check=False,
-                         warm=gp.WarmStart(cuda(np.zeros(oracle.ws_nparams(), np.float32)), cuda(sketch(20))))
+    warm = gp.WarmStart(cuda(np.zeros(oracle.ws_nparams(), np.float32)), cuda(sketch(20)))
+    with gp.Handle(20, 3000, 2) as h:
+        r = gp.gspca_fit(h.h, torch.zeros((20, 10), device="cuda"), 2, algo="nipals", check=False, warm=warm)
+        assert r.status == gp.GSPCA_ERR_NOT_SUPPORTED
+        r = gp.gspca_fit(h.h, torch.zeros((20, 2049), device="cuda"), 2, algo="gs", check=False, warm=warm)
         assert r.status == gp.GSPCA_ERR_NOT_SUPPORTED
 
 
