@@ -123,6 +123,10 @@ typedef struct {
     const gspca_warm_start *warm;  /* host pointer, nullable: learned warm start (GS-PCA only;
                                gspca_fit, gspca_fit_host, gspca_fit_batched[_async]).  The first
                                call on a handle that uses it grows the handle's workspace. */
+    int resident;           /* single-problem GS-PCA: 0 = automatic, 1 = keep each CTA's rows of the
+                               score factors and slices of the loading factors in shared memory
+                               (fewer pipeline stages for R), 2 = keep them in global memory.  The
+                               results do not depend on it. */
 } gspca_opts;
 
 /* Per-call record of the last fit on a handle (host memory). */

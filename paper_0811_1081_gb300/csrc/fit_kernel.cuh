@@ -86,6 +86,9 @@ struct FitArgs {
     int max_slice;            // shared-memory length of the N slice (>= n1 - n0)
     int redundant_max;        // reduce k-vectors in every CTA when k <= this
     int narrow;               // 1: the loading pass is pass_lds (N <= 1024, no CTA ring)
+    int res_rows;             // > 0: this CTA's rows of V (res_rows) and its slices of U and W
+                              // (max_slice each) live in shared memory at byte res_off
+    int res_off;
     // learned warm start (GS-PCA; all null when off)
     const float* ws_net;      // kWsParams network parameters
     const float* ws_G;        // sketch, M x 16 row-major
@@ -721,6 +724,10 @@ __device__ __forceinline__ bool pass_narrow(const FitArgs& f, SmemFit& sm, int p
 
 // ------------------------------------------------------------------ small products
 
+// The factor products below read A with generic loads: A is this CTA's own
+// rows of V or slice of U / W (written only by this CTA, in shared memory when
+// resident) or the read-only sketch.
+//
 // Row-major k-column factors (V, U, W) with a power-of-two leading dimension
 // lda in [4, 128] are read as float4 chunks: lda / 4 lanes cover one row, a
 // warp load covers 32 / (lda / 4) consecutive rows (512 contiguous bytes), and
@@ -750,7 +757,7 @@ __device__ __forceinline__ void rows_times_matrix_vec(const float* A, int lda, i
             const int r = rb + u * rpw + sub;
             const bool ok = r < r1;
             yr[u] = ok ? y(r) : 0.f;
-            a[u] = (ok && live) ? __ldcg(reinterpret_cast<const float4*>(A + (size_t)r * lda) + cq)
+            a[u] = (ok && live) ? reinterpret_cast<const float4*>(A + (size_t)r * lda)[cq]
                                 : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
@@ -794,7 +801,7 @@ __device__ __forceinline__ void matrix_times_vector_vec(const float* A, int lda,
             const int r = rb + u * rpw + sub;
             const bool ok = r < r1;
             pv[u] = (ok && cq == 0) ? pre(r) : 0.f;
-            a[u] = (ok && live) ? __ldcg(reinterpret_cast<const float4*>(A + (size_t)r * lda) + cq)
+            a[u] = (ok && live) ? reinterpret_cast<const float4*>(A + (size_t)r * lda)[cq]
                                 : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
@@ -835,7 +842,7 @@ __device__ __forceinline__ void rows_times_matrix(const float* A, int lda, int r
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int j = j0 + lane + 32 * q;
-                    a[i][q] = (ok && j < kk) ? ldcg(A + (size_t)r * lda + j) : 0.f;
+                    a[i][q] = (ok && j < kk) ? A[(size_t)r * lda + j] : 0.f;
                 }
             }
 #pragma unroll
@@ -884,7 +891,7 @@ __device__ __forceinline__ void matrix_times_vector(const float* A, int lda, int
 #pragma unroll
                 for (int q = 0; q < MAXJ; ++q) {
                     const int r = rb + nw * i, j = j0 + lane + 32 * q;
-                    a[i][q] = (r < r1 && j < kk) ? ldcg(A + (size_t)r * lda + j) : 0.f;
+                    a[i][q] = (r < r1 && j < kk) ? A[(size_t)r * lda + j] : 0.f;
                 }
 #pragma unroll
             for (int q = 0; q < MAXJ; ++q) {
@@ -1472,6 +1479,20 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
     const float tolf = (float)f.tol;
     (void)warp;
     (void)lane;
+    // This CTA's rows of V and slices of U and W: in shared memory when resident
+    // (V and U are also written to global memory when a component finishes).
+    float* Vl = f.V;
+    float* Ul = f.U;
+    float* Wl = f.W;
+    if (f.res_rows > 0) {
+        float* rbase = reinterpret_cast<float*>(dyn_smem + f.res_off);
+        const int nres = f.res_rows * f.ldv + f.max_slice * (f.ldu + f.ldw);
+        for (int i = tid; i < nres; i += T) rbase[i] = 0.f;
+        Vl = rbase - (size_t)r0 * f.ldv;
+        Ul = rbase + (size_t)f.res_rows * f.ldv - (size_t)n0 * f.ldu;
+        Wl = rbase + (size_t)f.res_rows * f.ldv + (size_t)f.max_slice * f.ldu - (size_t)n0 * f.ldw;
+        __syncthreads();
+    }
 
     int status = kStOK, found = K;
     long long total = 0;
@@ -1545,7 +1566,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
             write_scalar(f, g, 0, sc);
         }
         if (gs && k > 0)  // Gram row (V^T v_{k-1})_j over this CTA's rows
-            rows_times_matrix(f.V, f.ldv, r0, r1, k, [&](int r) { return f.V[(size_t)r * f.ldv + (k - 1)]; },
+            rows_times_matrix(Vl, f.ldv, r0, r1, k, [&](int r) { return Vl[(size_t)r * f.ldv + (k - 1)]; },
                               pA + N, sm);
         if (defl) fence_proxy_async_global();
         GS_SYNC();
@@ -1642,8 +1663,8 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                 const float lpf = (float)lam_prev;
                 for (int e = tid; e < (n1 - n0) * k; e += T) {
                     const int n = n0 + e / k, jj = e % k;
-                    const float un = f.U[(size_t)n * f.ldu + km];
-                    float* w = f.W + (size_t)n * f.ldw + jj;
+                    const float un = Ul[(size_t)n * f.ldu + km];
+                    float* w = Wl + (size_t)n * f.ldw + jj;
                     if (jj < km)
                         *w = fmaf(-lpf * un, kb[jj], *w);
                     else
@@ -1654,7 +1675,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
             // u_pre = s0; a = U_(k)^T u_pre; ut = (u_pre - U a) / ||x||^2
             for (int n = n0 + tid; n < n1; n += T) f.upre[n] = sv[n - n0];
             __syncthreads();
-            rows_times_matrix(f.U, f.ldu, n0, n1, k, [&](int n) { return sv[n - n0]; }, pB, sm);
+            rows_times_matrix(Ul, f.ldu, n0, n1, k, [&](int n) { return sv[n - n0]; }, pB, sm);
             GS_SYNC();
             if (small_k) {
                 gather_reduce(f, sm, G, 0, 0, 0, f.partB, f.LB, k, ident, ka);
@@ -1665,7 +1686,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                 __syncthreads();
             }
             matrix_times_vector(
-                f.U, f.ldu, n0, n1, k, ka, [&](int n) { return sv[n - n0]; },
+                Ul, f.ldu, n0, n1, k, ka, [&](int n) { return sv[n - n0]; },
                 [&](int n, float s, float p) {
                     const float un = (p - s) * xx_inv;
                     f.ut[(size_t)nb * N + n] = un;
@@ -1739,7 +1760,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
             }
             write_scalar(f, g, 0, sc);
             if (gs && k > 0)  // b' = V_(k)^T v' over this CTA's rows
-                rows_times_matrix(f.V, f.ldv, r0, r1, k, [&](int r) { return f.vraw[r]; }, pA + N, sm);
+                rows_times_matrix(Vl, f.ldv, r0, r1, k, [&](int r) { return f.vraw[r]; }, pA + N, sm);
             PHASE_MARK(3);
             GS_SYNC();
             PHASE_MARK(4);
@@ -1775,17 +1796,17 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                 PHASE_MARK(6);
                 ff l2 = ff_zero();
                 matrix_times_vector(
-                    f.V, f.ldv, r0, r1, k, kb, [&](int r) { return ldcg(f.vraw + r); },
+                    Vl, f.ldv, r0, r1, k, kb, [&](int r) { return ldcg(f.vraw + r); },
                     [&](int r, float s, float p) {
                         const float vc = p - s;
                         f.vcorr[r] = vc;
                         l2 = ff_add(l2, ff_sqr(vc));
                     });
                 matrix_times_vector(
-                    f.W, f.ldw, n0, n1, k, kb, [&](int n) { return sv[n - n0]; },
+                    Wl, f.ldw, n0, n1, k, kb, [&](int n) { return sv[n - n0]; },
                     [&](int n, float s, float p) { f.upre[n] = p - s; });
                 __syncthreads();
-                rows_times_matrix(f.U, f.ldu, n0, n1, k, [&](int n) { return f.upre[n]; }, pB, sm);
+                rows_times_matrix(Ul, f.ldu, n0, n1, k, [&](int n) { return f.upre[n]; }, pB, sm);
                 l2 = block_sum_ff(l2, sm);
                 write_scalar(f, g, 1, l2);
                 PHASE_MARK(7);
@@ -1830,7 +1851,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                 }
             } else {
                 matrix_times_vector(
-                    f.U, f.ldu, n0, n1, k, ka, [&](int n) { return ldcg(f.upre + n); },
+                    Ul, f.ldu, n0, n1, k, ka, [&](int n) { return ldcg(f.upre + n); },
                     [&](int n, float s, float p) {
                         const float un = (p - s) * nscale;
                         f.ut[(size_t)nbuf * N + n] = un;
@@ -1849,14 +1870,17 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                 if (stop == 3 && status == kStOK) status = kStNotConverged;
                 // finalize component k: V(k), U(k), lambda_k, iters_k
                 const float vinv = __fdiv_rn(1.f, __fsqrt_rn(l2f));
-                if (gs) {
-                    const float* src = (k > 0) ? f.vcorr : f.vraw;
-                    for (int r = r0 + tid; r < r1; r += T) f.V[(size_t)r * f.ldv + k] = src[r] * vinv;
-                } else {
-                    for (int r = r0 + tid; r < r1; r += T) f.V[(size_t)r * f.ldv + k] = f.vraw[r] * inv_nu;
+                const bool res = f.res_rows > 0;
+                for (int r = r0 + tid; r < r1; r += T) {
+                    const float v = gs ? ((k > 0) ? f.vcorr[r] : f.vraw[r]) * vinv : f.vraw[r] * inv_nu;
+                    f.V[(size_t)r * f.ldv + k] = v;
+                    if (res) Vl[(size_t)r * f.ldv + k] = v;
                 }
-                for (int n = n0 + tid; n < n1; n += T)
-                    f.U[(size_t)n * f.ldu + k] = ldcg(f.ut + (size_t)buf * N + n) * inv_nu;
+                for (int n = n0 + tid; n < n1; n += T) {
+                    const float u = ldcg(f.ut + (size_t)buf * N + n) * inv_nu;
+                    f.U[(size_t)n * f.ldu + k] = u;
+                    if (res) Ul[(size_t)n * f.ldu + k] = u;
+                }
                 lam_prev = ff_to_double(lamff);
                 if (g == 0 && tid == 0) {
                     f.lam[k] = lam_prev;

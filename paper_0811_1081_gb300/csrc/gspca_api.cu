@@ -49,7 +49,7 @@ gspca_status check_fit_args(gspca_t h, const void* X, gspca_layout layout, long 
     }
     if (opts) {
         if (opts->center < 0 || opts->center > 2 || opts->grid_ctas < 0 || opts->timeout_s < 0 ||
-            opts->test_stall < 0 || opts->test_stall > 1)
+            opts->test_stall < 0 || opts->test_stall > 1 || opts->resident < 0 || opts->resident > 2)
             return GSPCA_ERR_INVALID_ARG;
         if (opts->iters_lock)
             for (int k = 0; k < K; ++k)
@@ -100,7 +100,8 @@ gspca_status enqueue_fit(gspca_t h, cudaStream_t s, const float* X, gspca_layout
         if (ws != GSPCA_OK) return ws;
     }
     Plan plan{};
-    GS_CUDA(plan_fit(h->device, h->num_sms, h->ws.G, M, N, K, cell_bytes(h->dtype), opts, &plan));
+    GS_CUDA(plan_fit(h->device, h->num_sms, h->ws.G, M, N, K, cell_bytes(h->dtype), algo == GSPCA_GS, h->ws.ld,
+                     opts, &plan));
     const int* lock_dev = nullptr;
     if (opts && opts->iters_lock) {
         GS_CUDA(cudaMemcpyAsync(h->ws.lock, opts->iters_lock, sizeof(int) * K, cudaMemcpyHostToDevice, s));

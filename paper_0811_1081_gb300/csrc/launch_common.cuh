@@ -20,14 +20,21 @@ constexpr int kRedundantMax = 128;      // k up to which every CTA reduces a k-v
 
 struct Plan {
     int cpt, ppr, G, S, ldk, max_slice, groups;
+    int res_rows;   // > 0: the factor rows and slices are kept in shared memory (see FitArgs)
+    size_t res;     // their bytes
     int cb;     // bytes of one cell of R: 16 (FP32 storage) or 8 (bfloat16 storage)
     bool warm;  // the kernel with the learned warm start
     size_t dyn;
 };
 
+// Largest resident factor block chosen automatically.
+constexpr size_t kResMaxBytes = 48 * 1024;
+
 // Shared memory after the ring: the CTA's slice of the pass result, two
 // k-vectors, and the slice of the learned start's second pass result.
-inline size_t vec_bytes(int ldk, int max_slice) { return sizeof(float) * (2 * (size_t)ldk + 2 * (size_t)max_slice); }
+inline size_t vec_bytes(int ldk, int max_slice) {
+    return (sizeof(float) * (2 * (size_t)ldk + 2 * (size_t)max_slice) + 15) / 16 * 16;
+}
 
 // Bytes of one cell of R (4 rows x 1 column) for a storage type.
 inline int cell_bytes(gspca_dtype dt) { return dt == GSPCA_BF16 ? 8 : 16; }
@@ -83,8 +90,10 @@ inline cudaError_t fit_attrs_any(int cpt, int cb, bool warm, size_t dyn, int* bp
 
 // Grid size, ring depth and shared memory for one problem.  Gcap bounds the
 // grid (the partial buffers' row count).
-inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int K, int cb, const gspca_opts* opts,
-                            Plan* p) {
+// ldf: leading dimension of the factor workspaces V, U, W the kernel indexes with
+// (the workspace's, which may exceed ws_ld(K)); it sizes the resident block.
+inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int K, int cb, bool gs, int ldf,
+                            const gspca_opts* opts, Plan* p) {
     p->cb = cb;
     p->warm = opts && opts->warm;
     p->cpt = cpt_for(N);
@@ -100,13 +109,24 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
     p->ldk = ws_ld(K);
     p->max_slice = (N + G - 1) / G + 1;
     const size_t vec = vec_bytes(p->ldk, p->max_slice);
+    // GS-PCA: keep this CTA's rows of V and slices of U and W in shared memory when
+    // they take at most kResMaxBytes (auto) or when asked to (opts->resident = 1)
+    const int np_cta = (np + G - 1) / G;
+    const size_t res = sizeof(float) * ((size_t)4 * np_cta * ldf + 2 * (size_t)p->max_slice * ldf);
+    const int rmode = opts ? opts->resident : 0;
+    p->res_rows = 0;
+    p->res = 0;
+    if (gs && rmode != 2 && (rmode == 1 || res <= kResMaxBytes)) {
+        p->res_rows = 4 * np_cta;
+        p->res = res;
+    }
     int optin = 0;
     cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (e != cudaSuccess) return e;
     int bps = 0, st = 0;
     e = fit_attrs_any(p->cpt, cb, p->warm, vec, &bps, &st);
     if (e != cudaSuccess) return e;
-    const long avail = (long)optin - st - (long)vec - 1024;
+    const long avail = (long)optin - st - (long)vec - (long)p->res - 1024;
     // Preferred: the two-group loading pass with one panel per ring stage and an
     // even stage count; otherwise one group with PPR panels per stage.
     p->groups = 1;
@@ -124,7 +144,7 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
         if (S < 2) S = 0;
     }
     p->S = S;
-    p->dyn = vec + (size_t)S * stage;
+    p->dyn = vec + p->res + (size_t)S * stage;
     e = fit_attrs_any(p->cpt, cb, p->warm, p->dyn, &bps, &st);
     if (e != cudaSuccess) return e;
     if (bps < 1) return cudaErrorInvalidConfiguration;
@@ -196,7 +216,9 @@ inline FitArgs make_args(const Workspace& w, const Plan& p, int M, int N, int K,
     a.timing = nullptr;
     a.tma_stages = p.S;
     a.dot_groups = p.groups;
-    a.ring_bytes = (int)(p.dyn - vec_bytes(p.ldk, p.max_slice));
+    a.ring_bytes = (int)(p.dyn - vec_bytes(p.ldk, p.max_slice) - p.res);
+    a.res_rows = p.res_rows;
+    a.res_off = (int)(p.dyn - p.res);  // after the ring and the vectors
     a.ldk = p.ldk;
     a.max_slice = p.max_slice;
     a.redundant_max = kRedundantMax;

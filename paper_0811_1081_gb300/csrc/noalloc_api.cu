@@ -77,7 +77,7 @@ extern "C" gspca_status gspca_fit_noalloc(void* stream, const float* X, gspca_la
     // launch shape first (it fixes the grid, hence the partial buffers), then
     // the workspace for exactly this problem, checked against the array's size
     Plan plan{};
-    if (plan_fit(dev, sms, sms, M, N, K, cell_bytes(GSPCA_F32), opts, &plan) != cudaSuccess) return GSPCA_ERR_CUDA;
+    if (plan_fit(dev, sms, sms, M, N, K, cell_bytes(GSPCA_F32), algo == GSPCA_GS, ws_ld(K), opts, &plan) != cudaSuccess) return GSPCA_ERR_CUDA;
     const WsDims dims{(long)(M + 3) / 4 * 4, N, K, plan.G};
     if (carve(nullptr, dims).bytes > (size_t)GSPCA_NOALLOC_SCRATCH_BYTES) return GSPCA_ERR_NOT_SUPPORTED;
     const Workspace w = carve(scratch, dims);

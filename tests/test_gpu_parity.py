@@ -255,3 +255,22 @@ def test_full_size_10000x2000(gp):
     for k in range(3):
         assert abs(lam[k] - ref.lam[k]) <= SIG_REL * ref.lam[k]
         assert angle(P[:, k], ref.P[:, k]) <= ANGLE
+
+
+@pytest.mark.parametrize("shape", [(1003, 517, 6), (10000, 2000, 4), (64, 4097, 3)])
+def test_resident_factors_do_not_change_results(gp, shape):
+    """Keeping the factor rows/slices in shared memory or in global memory is a placement
+    choice only: the two fits are bit-identical."""
+    import torch
+
+    M, N, K = shape
+    X32 = synth.planted(M, N, 5.0, 0.85, 0.01, (31, M, N)).X.astype(np.float32)
+    Xd = torch.from_numpy(X32).cuda()
+    outs = []
+    with gp.Handle(M, N, K) as h:
+        for mode in (1, 2):
+            r = h.fit(Xd, K, tol=1e-6, max_iter=1000, algo="gs", want_R=True, resident=mode)
+            torch.cuda.synchronize()
+            outs.append([t.cpu().numpy() for t in (r.T, r.P, r.lam, r.iters, r.R)])
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
