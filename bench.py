@@ -39,12 +39,18 @@ UNIT = "components/s"
 FALLBACK_HBM_GBS = 6800.0
 
 
-def kernel_name(N):
-    """The instantiation of the persistent fit kernel for N columns (columns per thread)."""
+def kernel_name(N, storage="f32"):
+    """The instantiation of the persistent fit kernel for N columns (columns per thread),
+    the storage type of R, without the learned warm start."""
     cpt = 1
     while cpt * 512 < N:
         cpt *= 2
-    return f"fit_kernel<{cpt}>"
+    return f"fit_kernel<{cpt}, {'float' if storage == 'f32' else '__nv_bfloat16'}, false>"
+
+
+def profile_stem(kernel):
+    """File-name form of a kernel name: fit_kernel<4, float, false> -> fit_kernel_4_float_false."""
+    return kernel.replace("<", "_").replace(">", "").replace(", ", "_")
 
 
 def source_sha():
@@ -63,8 +69,7 @@ def source_sha():
 def profiled_traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary
     (profiles/<kernel>_<workload>.md), or None when it is absent or was taken on other sources."""
-    name = kernel.replace("<", "_").replace(">", "")
-    p = os.path.join(ROOT, "profiles", f"{name}_{workload}.md")
+    p = os.path.join(ROOT, "profiles", f"{profile_stem(kernel)}_{workload}.md")
     if not os.path.exists(p):
         return None, None
     vals = {}
@@ -367,6 +372,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the secondary 256-problem batched measurement")
+    ap.add_argument("--no-other-algo", action="store_true",
+                    help="skip the secondary measurement of the other algorithm on the same workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -420,7 +427,7 @@ def main():
 
     # roofline of the persistent kernel: algorithmic bytes / its event-timed duration
     peak, peak_src = measured_peaks()
-    kname = kernel_name(N)
+    kname = kernel_name(N, args.storage)
     traffic, traffic_src = profiled_traffic(kname, w.name)
     if traffic_src:
         traffic_src = os.path.relpath(traffic_src, ROOT) + (" (sources changed since: null)" if traffic is None else "")
@@ -469,6 +476,29 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms)},
     }
+    # orthogonality of the loadings (Sec. 2.3: GS keeps P^T P = I, NIPALS loses it)
+    Pd = r.P.double()
+    eye = torch.eye(K, dtype=torch.float64, device=dev)
+    line["orthogonality_max_abs_PtP_minus_I"] = float((Pd.t() @ Pd - eye).abs().max().item())
+    if not args.no_other_algo:
+        other = "nipals" if args.algo == "gs" else "gs"
+        for _ in range(2):
+            h.fit(Xd, K, tol=w.tol, max_iter=w.max_iter, algo=other)
+        o_ms = []
+        for i in range(3):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ro = h.fit(Xd, K, tol=w.tol, max_iter=w.max_iter, algo=other)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            o_ms.append(a.elapsed_time(b))
+        Po = ro.P.double()
+        line["other_algorithm"] = {
+            "algo": other, "value": K / (statistics.mean(o_ms) / 1e3), "unit": UNIT, "ms": statistics.mean(o_ms),
+            "iters_total_per_fit": ro.info["total_iters"], "status": gp.status_string(ro.status),
+            "orthogonality_max_abs_PtP_minus_I": float((Po.t() @ Po - eye).abs().max().item()),
+            "alg_gbs": ro.info["alg_bytes"] / ro.info["kernel_ms"] / 1e6}
     if not args.no_batched:
         line["batched"] = bench_batched(gp, dev, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
