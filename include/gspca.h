@@ -127,6 +127,9 @@ typedef struct {
                                score factors and slices of the loading factors in shared memory
                                (fewer pipeline stages for R), 2 = keep them in global memory.  The
                                results do not depend on it. */
+    int load_path;          /* single-problem fit: how the passes read R; 0 = automatic, 1 = through
+                               the shared-memory ring of TMA bulk copies where it fits, 2 = straight
+                               into registers.  The results do not depend on it. */
 } gspca_opts;
 
 /* Per-call record of the last fit on a handle (host memory). */

@@ -135,7 +135,10 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
     int S = avail > 0 ? (int)(avail / (long)stage) : 0;
     if (S > kMaxStages) S = kMaxStages;
     S &= ~1;
-    if (p->cpt >= 2 && p->cpt <= 4 && S >= 4) {
+    const int lpath = opts ? opts->load_path : 0;
+    if (lpath == 2) {
+        S = 0;  // register loads
+    } else if (p->cpt >= 2 && p->cpt <= 4 && S >= 4) {
         p->groups = 2;
     } else {
         stage = (size_t)p->ppr * panel;
