@@ -1429,6 +1429,120 @@ __device__ __noinline__ bool ws_select(const FitArgs& f, const Team& tm, SmemFit
     return true;
 }
 
+// The first pass of a component (and of the zero-column restart): the optional
+// deflation of component kprev (Eq. 3), R <- R - (lamf V(:, kprev)) u^T with u =
+// u_in * inv_nu, stored as it goes; the start column R(:, kcol) after it, row by
+// row; s = R^T R(:, kcol) (-> pA) while each panel is in registers, and *sc =
+// ||R(:, kcol)||^2 over this CTA's rows.  No CTA barrier per round: every
+// thread reads the start column's cells itself (the same address in every lane)
+// and deflates them exactly as their owner does, and the owner stores column
+// kcol only after the last round, so no thread ever reads an already deflated
+// cell of it.  Register loads; warps stream their panels independently.
+template <int CPT, class E>
+__device__ __forceinline__ void pass_start_col(const FitArgs& f, SmemFit& sm, int p0, int p1, int kcol, bool deflate,
+                                            float lamf, int kprev, const float* u_in, float inv_nu, float* pA,
+                                            ff* sc) {
+    constexpr int PPR = PassShape<CPT>::PPR;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, T = blockDim.x, N = f.N;
+    const size_t ldp = (size_t)f.ldp;
+    float uc[CPT], sacc[CPT];
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+        const int c = tid + i * T;
+        uc[i] = (deflate && c < N) ? ldcg(u_in + c) * inv_nu : 0.f;
+        sacc[i] = 0.f;
+    }
+    const float uk = deflate ? ldcg(u_in + kcol) * inv_nu : 0.f;
+    ff my = ff_zero();
+    for (int pb = p0; pb < p1; pb += PPR) {
+        float4 d[PPR][CPT], dk[PPR];
+#pragma unroll
+        for (int pp = 0; pp < PPR; ++pp) {
+            const int p = pb + pp;
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) {
+                const int c = tid + i * T;
+                d[pp][i] = (p < p1 && c < N) ? Cell<E>::ldg(f.R, (size_t)p * ldp + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            dk[pp] = p < p1 ? Cell<E>::ldg(f.R, (size_t)p * ldp + kcol) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (deflate) {
+#pragma unroll
+            for (int pp = 0; pp < PPR; ++pp) {
+                const int p = pb + pp;
+                float cf[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int row = 4 * p + q;
+                    cf[q] = (p < p1 && row < f.M) ? lamf * f.V[(size_t)row * f.ldv + kprev] : 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < CPT; ++i) {
+                    const int c = tid + i * T;
+                    float4 v = d[pp][i];
+                    v.x = fmaf(-cf[0], uc[i], v.x);
+                    v.y = fmaf(-cf[1], uc[i], v.y);
+                    v.z = fmaf(-cf[2], uc[i], v.z);
+                    v.w = fmaf(-cf[3], uc[i], v.w);
+                    v = Cell<E>::quant(v);
+                    d[pp][i] = v;
+                    if (p < p1 && c < N && c != kcol) Cell<E>::stg(f.R, (size_t)p * ldp + c, v);
+                }
+                float4 v = dk[pp];
+                v.x = fmaf(-cf[0], uk, v.x);
+                v.y = fmaf(-cf[1], uk, v.y);
+                v.z = fmaf(-cf[2], uk, v.z);
+                v.w = fmaf(-cf[3], uk, v.w);
+                dk[pp] = Cell<E>::quant(v);
+            }
+        }
+        if (tid == 0)
+#pragma unroll
+            for (int pp = 0; pp < PPR; ++pp) {
+                my = ff_add(my, ff_sqr(dk[pp].x));
+                my = ff_add(my, ff_sqr(dk[pp].y));
+                my = ff_add(my, ff_sqr(dk[pp].z));
+                my = ff_add(my, ff_sqr(dk[pp].w));
+            }
+#pragma unroll
+        for (int i = 0; i < CPT; ++i)
+#pragma unroll
+            for (int pp = 0; pp < PPR; ++pp) {
+                const float4 v = d[pp][i];
+                sacc[i] = fmaf(v.x, dk[pp].x, sacc[i]);
+                sacc[i] = fmaf(v.y, dk[pp].y, sacc[i]);
+                sacc[i] = fmaf(v.z, dk[pp].z, sacc[i]);
+                sacc[i] = fmaf(v.w, dk[pp].w, sacc[i]);
+            }
+    }
+    if (tid == 0) sm.sff[3] = my;
+    __syncthreads();  // every thread has read column kcol's cells
+    if (deflate && warp == 0) {
+        // column kcol, deflated as every thread deflated it above
+        for (int p = p0 + lane; p < p1; p += 32) {
+            float4 v = Cell<E>::ldg(f.R, (size_t)p * ldp + kcol);
+            float cf[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = 4 * p + q;
+                cf[q] = row < f.M ? lamf * f.V[(size_t)row * f.ldv + kprev] : 0.f;
+            }
+            v.x = fmaf(-cf[0], uk, v.x);
+            v.y = fmaf(-cf[1], uk, v.y);
+            v.z = fmaf(-cf[2], uk, v.z);
+            v.w = fmaf(-cf[3], uk, v.w);
+            Cell<E>::stg(f.R, (size_t)p * ldp + kcol, Cell<E>::quant(v));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+        const int c = tid + i * T;
+        if (c < N) pA[c] = sacc[i];
+    }
+    *sc = sm.sff[3];
+    __syncthreads();
+}
+
 // (Re)initialise this CTA's ring: S stages of ppr panels of panel_bytes each.
 // Must be called with no copy in flight.
 __device__ __forceinline__ void ring_setup(Ring& rg, SmemFit& sm, unsigned char* dyn_smem, int S, int ppr,
@@ -1448,6 +1562,14 @@ __device__ __forceinline__ void ring_setup(Ring& rg, SmemFit& sm, unsigned char*
     rg.mbar = sm.mbar;
     rg.issued = rg.used = 0;
 }
+
+// Which first pass a team uses: the barrier-free one (pass_start_col) in the
+// single-problem kernel; the batched kernel keeps row_pass<kPassCol>, whose
+// register needs fit its larger state without spills.
+template <class Team>
+constexpr bool kStartColPass = false;
+template <>
+constexpr bool kStartColPass<TeamGrid> = true;
 
 // Fit one problem (f) with a team of CTAs.  The caller provides the
 // degenerate threshold and this CTA's shared memory; the ring must be set up
@@ -1546,22 +1668,27 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
             PHASE_MARK(12);
         }
         if (!cand) {
+            if constexpr (kStartColPass<Team>) {
+                pass_start_col<CPT, E>(f, sm, p0, p1, k, defl, lamf, k - 1, f.ut + (size_t)buf * N, inv_nu, pA,
+                                       &sc);
+            } else {
 #pragma unroll
-            for (int i = 0; i < CPT; ++i) {
-                const int c = tid + i * T;
-                uc[i] = (defl && c < N) ? ldcg(f.ut + (size_t)buf * N + c) * inv_nu : 0.f;
-            }
-            if (!row_pass<CPT, kPassCol, E>(f, sm, rg, p0, p1, uc, k, defl, lamf, k - 1, sacc, sc)) {
-                if (tm.fail(f)) {
-                    alive = false;
-                    goto leave;
+                for (int i = 0; i < CPT; ++i) {
+                    const int c = tid + i * T;
+                    uc[i] = (defl && c < N) ? ldcg(f.ut + (size_t)buf * N + c) * inv_nu : 0.f;
                 }
-                sc = ff{__int_as_float(0x7fc00000), 0.f};
-            }
+                if (!row_pass<CPT, kPassCol, E>(f, sm, rg, p0, p1, uc, k, defl, lamf, k - 1, sacc, sc)) {
+                    if (tm.fail(f)) {
+                        alive = false;
+                        goto leave;
+                    }
+                    sc = ff{__int_as_float(0x7fc00000), 0.f};
+                }
 #pragma unroll
-            for (int i = 0; i < CPT; ++i) {
-                const int c = tid + i * T;
-                if (c < N) pA[c] = sacc[i];
+                for (int i = 0; i < CPT; ++i) {
+                    const int c = tid + i * T;
+                    if (c < N) pA[c] = sacc[i];
+                }
             }
             write_scalar(f, g, 0, sc);
         }
@@ -1629,18 +1756,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                 status = kStDegenerate;
                 break;
             }
-            if (!row_pass<CPT, kPassCol, E>(f, sm, rg, p0, p1, uc, kcol, false, 0.f, 0, sacc, sc)) {
-                if (tm.fail(f)) {
-                    alive = false;
-                    goto leave;
-                }
-                sc = ff{__int_as_float(0x7fc00000), 0.f};
-            }
-#pragma unroll
-            for (int i = 0; i < CPT; ++i) {
-                const int c = tid + i * T;
-                if (c < N) pA[c] = sacc[i];
-            }
+            pass_start_col<CPT, E>(f, sm, p0, p1, kcol, false, 0.f, 0, f.ut, 0.f, pA, &sc);
             write_scalar(f, g, 0, sc);
             GS_SYNC();
             gather_reduce(f, sm, G, 1, 0, 0, f.partA, f.LA, nc1 + nk0, slice_then_k, rb);

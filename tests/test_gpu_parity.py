@@ -257,6 +257,29 @@ def test_full_size_10000x2000(gp):
         assert angle(P[:, k], ref.P[:, k]) <= ANGLE
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("shape", [(1003, 517, 6), (700, 2000, 4), (64, 4097, 3), (300, 7500, 3)])
+def test_load_path_gives_the_same_fit(gp, shape, storage):
+    """Reading R through the TMA ring or straight into registers: the same fit (the two-group
+    ring pass sums in another order, so the second run replays the first's iteration counts and
+    the results agree to FP32 rounding)."""
+    import torch
+
+    M, N, K = shape
+    X32 = synth.planted(M, N, 5.0, 0.85, 0.01, (37, M, N)).X.astype(np.float32)
+    Xd = torch.from_numpy(X32).cuda()
+    with gp.Handle(M, N, K, dtype=storage) as h:
+        a = h.fit(Xd, K, tol=1e-6, max_iter=1000, algo="gs", load_path=1)
+        lock = [int(v) for v in a.iters.cpu().numpy()]
+        b = h.fit(Xd, K, tol=1e-6, max_iter=1000, algo="gs", load_path=2, iters_lock=lock)
+        torch.cuda.synchronize()
+        la, lb = a.lam.cpu().numpy(), b.lam.cpu().numpy()
+        Pa, Pb = a.P.cpu().numpy().astype(np.float64), b.P.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(la - lb) <= 1e-5 * la)
+    for k in range(K):
+        assert angle(Pa[:, k], Pb[:, k]) <= 1e-4
+
+
 @pytest.mark.parametrize("shape", [(1003, 517, 6), (10000, 2000, 4), (64, 4097, 3)])
 def test_resident_factors_do_not_change_results(gp, shape):
     """Keeping the factor rows/slices in shared memory or in global memory is a placement
