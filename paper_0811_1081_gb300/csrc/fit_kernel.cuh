@@ -403,6 +403,117 @@ __device__ __forceinline__ bool row_pass(const FitArgs& f, SmemFit& sm, Ring& rg
     return all_ok != 0;
 }
 
+// bf_unpack through opaque instructions, so the compiler re-derives the values
+// instead of keeping an earlier unpacking of the same words alive.
+__device__ __forceinline__ float4 bf_unpack_again(uint2 w) {
+    uint32_t a, b, c, d;
+    asm volatile("shl.b32 %0, %1, 16;" : "=r"(a) : "r"(w.x));
+    asm volatile("and.b32 %0, %1, 0xffff0000;" : "=r"(b) : "r"(w.x));
+    asm volatile("shl.b32 %0, %1, 16;" : "=r"(c) : "r"(w.y));
+    asm volatile("and.b32 %0, %1, 0xffff0000;" : "=r"(d) : "r"(w.y));
+    return make_float4(__uint_as_float(a), __uint_as_float(b), __uint_as_float(c), __uint_as_float(d));
+}
+
+// Loading pass (kPassDot) for bfloat16 storage read straight into registers (up
+// to 4096 columns per CTA; wider rows would not fit the registers):
+// a cell stays packed (two 32-bit words) until it is used and is unpacked twice
+// (for R u' and for R^T v'), and the packed cells of the next round are loaded
+// before the current one is used, so two rounds of R are in flight in the
+// registers a FP32 round occupies.  Same arithmetic as row_pass<kPassDot>.
+// Input u' from u_in (N values), output: the CTA's s' partials in pA[0..N).
+template <int CPT>
+__device__ __noinline__ void pass_dot_reg_bf16(const FitArgs& f, SmemFit& sm, int p0, int p1, const float* u_in,
+                                               float* pA, ff* sc_out) {
+    constexpr int PPR = PassShape<CPT>::PPR;
+    constexpr int RPR = PassShape<CPT>::RPR;
+    constexpr int SH = 5 - Log2<RPR>::value;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int T = blockDim.x, N = f.N;
+    const size_t ldp = (size_t)f.ldp;
+    const uint2* Rw = static_cast<const uint2*>(f.R);
+    float uc[CPT], sacc[CPT];
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+        const int c = tid + i * T;
+        uc[i] = c < N ? ldcg(u_in + c) : 0.f;
+        sacc[i] = 0.f;
+    }
+    ff my = ff_zero();
+    uint2 nxt[PPR][CPT];
+    auto load = [&](int pb) {
+#pragma unroll
+        for (int pp = 0; pp < PPR; ++pp)
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) {
+                const int c = tid + i * T, p = pb + pp;
+                uint2 w = make_uint2(0u, 0u);
+                if (p < p1 && c < N)
+                    asm volatile("ld.global.cg.v2.u32 {%0,%1}, [%2];" : "=r"(w.x), "=r"(w.y) : "l"(Rw + (size_t)p * ldp + c));
+                nxt[pp][i] = w;
+            }
+    };
+    if (p0 < p1) load(p0);
+    int buf = 0;
+    for (int pb = p0; pb < p1; pb += PPR, buf ^= 1) {
+        uint2 cur[PPR][CPT];
+#pragma unroll
+        for (int pp = 0; pp < PPR; ++pp)
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) cur[pp][i] = nxt[pp][i];
+        if (pb + PPR < p1) load(pb + PPR);
+        float acc[RPR];
+#pragma unroll
+        for (int r = 0; r < RPR; ++r) acc[r] = 0.f;
+#pragma unroll
+        for (int i = 0; i < CPT; ++i)
+#pragma unroll
+            for (int pp = 0; pp < PPR; ++pp) {
+                const float4 d = bf_unpack(cur[pp][i]);
+                acc[pp * 4 + 0] = fmaf(d.x, uc[i], acc[pp * 4 + 0]);
+                acc[pp * 4 + 1] = fmaf(d.y, uc[i], acc[pp * 4 + 1]);
+                acc[pp * 4 + 2] = fmaf(d.z, uc[i], acc[pp * 4 + 2]);
+                acc[pp * 4 + 3] = fmaf(d.w, uc[i], acc[pp * 4 + 3]);
+            }
+        const float r = warp_multi_reduce<RPR>(acc, lane);
+        if ((lane & ((1 << SH) - 1)) == 0) sm.wsum[buf][warp][lane >> SH] = r;
+        __syncthreads();
+        float rs = 0.f;
+        if (lane < RPR)
+            for (int w = 0; w < nw; ++w) rs += sm.wsum[buf][w][lane];
+        if (warp == 0 && lane < RPR && pb + (lane >> 2) < p1) {
+            f.vraw[(size_t)pb * 4 + lane] = rs;
+            my = ff_add(my, ff_sqr(rs));
+        }
+        float rowv[RPR];
+#pragma unroll
+        for (int r2 = 0; r2 < RPR; ++r2) rowv[r2] = __shfl_sync(kFull, rs, r2);
+#pragma unroll
+        for (int i = 0; i < CPT; ++i)
+#pragma unroll
+            for (int pp = 0; pp < PPR; ++pp) {
+                // unpacked again rather than kept from the first use: the unpacked round
+                // would need twice the registers across the row reduction
+                const float4 d = bf_unpack_again(cur[pp][i]);
+                sacc[i] = fmaf(d.x, rowv[pp * 4 + 0], sacc[i]);
+                sacc[i] = fmaf(d.y, rowv[pp * 4 + 1], sacc[i]);
+                sacc[i] = fmaf(d.z, rowv[pp * 4 + 2], sacc[i]);
+                sacc[i] = fmaf(d.w, rowv[pp * 4 + 3], sacc[i]);
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+        const int c = tid + i * T;
+        if (c < N) pA[c] = sacc[i];
+    }
+    if (warp == 0) {
+        const ff t = warp_sum_ff(my);
+        if (lane == 0) sm.sff[3] = t;
+    }
+    __syncthreads();
+    *sc_out = sm.sff[3];
+    __syncthreads();
+}
+
 __device__ __forceinline__ void named_barrier(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
@@ -1853,7 +1964,15 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                     two_done = true;
                 }
             }
-            if (!two_done) {
+            bool packed = false;
+            if constexpr (Cell<E>::kBytes == 8 && kStartColPass<Team> && CPT <= 8) {
+                if (!two_done && rg.S == 0) {
+                    PHASE_MARK(2);
+                    pass_dot_reg_bf16<CPT>(f, sm, p0, p1, f.ut + (size_t)buf * N, pA, &sc);
+                    packed = true;
+                }
+            }
+            if (!two_done && !packed) {
 #pragma unroll
                 for (int i = 0; i < CPT; ++i) {
                     const int c = tid + i * T;

@@ -136,7 +136,10 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
     if (S > kMaxStages) S = kMaxStages;
     S &= ~1;
     const int lpath = opts ? opts->load_path : 0;
-    if (lpath == 2) {
+    // bfloat16 cells at 2049-4096 columns: the packed register pass (two rounds in
+    // flight) streams faster than the ring's few wide stages (measured on GB300)
+    const bool packed = cb == 8 && p->cpt == 8 && lpath == 0;
+    if (lpath == 2 || packed) {
         S = 0;  // register loads
     } else if (p->cpt >= 2 && p->cpt <= 4 && S >= 4) {
         p->groups = 2;
