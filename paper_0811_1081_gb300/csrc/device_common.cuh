@@ -233,7 +233,9 @@ struct GridBarrier {
                 }
             }
             fence_acq_rel_gpu();
-            *s_flag = ok && ld_relaxed_s32(abort) == 0;
+            // A full count means every CTA arrived; one that gave up elsewhere left
+            // without arriving, so the next wait sees its abort flag.
+            *s_flag = ok;
         }
         __syncthreads();
         return *s_flag != 0;
