@@ -130,6 +130,11 @@ typedef struct {
     int load_path;          /* single-problem fit: how the passes read R; 0 = automatic, 1 = through
                                the shared-memory ring of TMA bulk copies where it fits, 2 = straight
                                into registers.  The results do not depend on it. */
+    int gs_step;            /* single-problem GS-PCA with resident factors: 0 = automatic (the
+                               Gram-Schmidt step of an iteration takes two grid-wide reductions
+                               where that is numerically safe, by keeping Q = R U, Z = U^T W and
+                               V^T V up to date per component; otherwise three), 1 = always the
+                               three-reduction step of Sec. 2.3.  The two agree to FP32 rounding. */
 } gspca_opts;
 
 /* Per-call record of the last fit on a handle (host memory). */

@@ -58,7 +58,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("center", ctypes.c_int), ("iters_lock", ctypes.POINTER(ctypes.c_int)),
                 ("grid_ctas", ctypes.c_int), ("timeout_s", ctypes.c_double),
                 ("cluster_ctas", ctypes.c_int), ("batch_pass", ctypes.c_int), ("test_stall", ctypes.c_int),
-                ("warm", ctypes.POINTER(WarmStartC)), ("resident", ctypes.c_int), ("load_path", ctypes.c_int)]
+                ("warm", ctypes.POINTER(WarmStartC)), ("resident", ctypes.c_int), ("load_path", ctypes.c_int),
+                ("gs_step", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -149,10 +150,11 @@ class WarmStart:
 
 
 def _opts(center=0, iters_lock=None, grid_ctas=0, timeout_s=0.0, cluster_ctas=0, test_stall=0, batch_pass=0,
-          warm=None, resident=0, load_path=0):
+          warm=None, resident=0, load_path=0, gs_step=0):
     o = Opts()
     o.resident = int(resident)
     o.load_path = int(load_path)
+    o.gs_step = int(gs_step)
     o.batch_pass = int(batch_pass)
     o.test_stall = int(test_stall)
     o.center = int(center)
@@ -217,7 +219,8 @@ class FitResult:
 def gspca_fit(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="gs",
               center: int = 0, iters_lock=None, want_R: bool = False, grid_ctas: int = 0,
               timeout_s: float = 0.0, stream=None, check: bool = True, test_stall: int = 0,
-              warm: WarmStart | None = None, resident: int = 0, load_path: int = 0) -> FitResult:
+              warm: WarmStart | None = None, resident: int = 0, load_path: int = 0,
+              gs_step: int = 0) -> FitResult:
     """Fit K components of X (a float32 CUDA tensor, any 2-D strided layout).  `warm`: the
     learned warm start (GS-PCA); the result's ws_choice marks the components that used it."""
     import torch
@@ -240,7 +243,7 @@ def gspca_fit(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="
     choice = torch.zeros(K, device=dev, dtype=torch.int32) if warm is not None else None
     o, keep = _opts(center, iters_lock, grid_ctas, timeout_s, 0, test_stall,
                     warm=warm.c_struct(choice) if warm is not None else None, resident=resident,
-                    load_path=load_path)
+                    load_path=load_path, gs_step=gs_step)
     st = load().gspca_fit(ctypes.c_void_p(h), ctypes.c_void_p(stream), ctypes.c_void_p(X.data_ptr()),
                           layout, int(ldx), M, N, int(K), float(tol), int(max_iter), _ALGOS[algo],
                           ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(P.data_ptr()),

@@ -89,6 +89,11 @@ struct FitArgs {
     int res_rows;             // > 0: this CTA's rows of V (res_rows) and its slices of U and W
                               // (max_slice each) live in shared memory at byte res_off
     int res_off;
+    int gs2;                  // 1 (single-problem GS-PCA, FP32 storage, resident, K <= 64): the
+                              // resident block also holds this CTA's rows of Q = R_k U_(k) and the
+                              // matrices Z = U^T W and V^T V (ldk x ldk), kept up to date per component, and an
+                              // iteration may form a' and ||v' - V b'||^2 from them (two grid-wide
+                              // reductions per iteration instead of three)
     // learned warm start (GS-PCA; all null when off)
     const float* ws_net;      // kWsParams network parameters
     const float* ws_G;        // sketch, M x 16 row-major
@@ -112,12 +117,14 @@ struct __align__(16) SmemFit {
     ff ffq[kMaxWarps][4];
     ff sff[4];
     ff lamff;
+    ff lam2s;
     double dsc[4];
     double wsv[24];
     unsigned long long mbar[kMaxStages];
     int flag;
     int sel;
     int stop;
+    int step2;
     int mbar_live;
 #ifdef GSPCA_PHASE_TIMING
     unsigned long long tacc[16];
@@ -932,6 +939,55 @@ __device__ __forceinline__ void matrix_times_vector_vec(const float* A, int lda,
 // dst[j] = sum_{r in [r0, r1)} A[r*lda + j] * y(r) for j < kk, FP32 within the CTA.
 // A warp takes rows r0 + warp + 16 i (i < 8 per block) and issues every load
 // of the block (A and y) before using any of them.
+// rows_times_matrix of two matrices with the same rows and weights (kk <= 64):
+// dstA = A^T y and dstB = B^T y over rows [r0, r1) in one sweep and one
+// cross-warp sum; dstA's arithmetic is the general path's of rows_times_matrix.
+template <class Y>
+__device__ __forceinline__ void rows_times_two(const float* A, const float* B, int lda, int r0, int r1, int kk, Y y,
+                                               float* dstA, float* dstB, SmemFit& sm) {
+    constexpr int MAXR = 8;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    float accA[2] = {0.f, 0.f}, accB[2] = {0.f, 0.f};
+    for (int rb = r0 + warp; rb < r1; rb += nw * MAXR) {
+        float a[MAXR][2], b[MAXR][2], yr[MAXR];
+#pragma unroll
+        for (int i = 0; i < MAXR; ++i) {
+            const int r = rb + nw * i;
+            const bool ok = r < r1;
+            yr[i] = ok ? y(r) : 0.f;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int j = lane + 32 * q;
+                a[i][q] = (ok && j < kk) ? A[(size_t)r * lda + j] : 0.f;
+                b[i][q] = (ok && j < kk) ? B[(size_t)r * lda + j] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < MAXR; ++i)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                accA[q] = fmaf(a[i][q], yr[i], accA[q]);
+                accB[q] = fmaf(b[i][q], yr[i], accB[q]);
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        sm.tmpf[warp][lane + 32 * q] = accA[q];
+        sm.tmpf[warp][64 + lane + 32 * q] = accB[q];
+    }
+    __syncthreads();
+    for (int t = tid; t < 2 * kk; t += blockDim.x) {
+        const int c = t < kk ? t : 64 + (t - kk);
+        float s = 0.f;
+        for (int w = 0; w < nw; ++w) s += sm.tmpf[w][c];
+        if (t < kk)
+            dstA[t] = s;
+        else
+            dstB[t - kk] = s;
+    }
+    __syncthreads();
+}
+
 template <class Y>
 __device__ __forceinline__ void rows_times_matrix(const float* A, int lda, int r0, int r1, int kk, Y y, float* dst,
                                                   SmemFit& sm) {
@@ -1052,10 +1108,11 @@ __device__ __forceinline__ ff block_sum_ff(ff v, SmemFit& sm) {
 // before any of them is used (one L2 round trip).  Warp w loads rows w, w+16,
 // ...; lane l loads columns l and l+32 of a block; a thread sums its rows in
 // FP32, the 16 warp sums of a column combine in a fixed float-float butterfly.
-template <class Col>
+template <int MAXJ = 2, class Col>
 __device__ __forceinline__ void gather_reduce(const FitArgs& f, SmemFit& sm, int G, int nq, int s0, int s1,
                                               const float* part, int L, int nv, Col col, float* out) {
-    constexpr int MAXI = 10, MAXJ = 2, NW = kMaxWarps;
+    static_assert(MAXJ == 2 || MAXJ == 4, "32 MAXJ values per round trip");
+    constexpr int MAXI = 10, NW = kMaxWarps;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     float2 q0 = make_float2(0.f, 0.f), q1 = make_float2(0.f, 0.f);
     if (t < G) {
@@ -1091,8 +1148,9 @@ __device__ __forceinline__ void gather_reduce(const FitArgs& f, SmemFit& sm, int
             }
         }
         __syncthreads();
-        {  // warp w combines columns 4w..4w+3 of the block: lane = 8*c + h
-            const int c = 4 * warp + (lane >> 3), h = lane & 7;
+        for (int cb = 0; cb < 32 * MAXJ && vb + cb < nv; cb += 64) {
+            // warp w combines columns cb + 4w .. cb + 4w + 3 of the block: lane = 8*c + h
+            const int c = cb + 4 * warp + (lane >> 3), h = lane & 7;
             ff a = ff_add(ff{sm.tmpf[h][c], 0.f}, ff{sm.tmpf[h + 8][c], 0.f});
             a = ff_add(a, ff_shfl_xor(a, 1));
             a = ff_add(a, ff_shfl_xor(a, 2));
@@ -1682,6 +1740,11 @@ constexpr bool kStartColPass = false;
 template <>
 constexpr bool kStartColPass<TeamGrid> = true;
 
+// The two-reduction GS step (FitArgs::gs2) exists in the single-problem kernel
+// for FP32 storage, up to 4096 columns per CTA, without the learned warm start.
+template <int CPT, class E, bool WARM, class Team>
+constexpr bool kGs2Step = kStartColPass<Team> && !WARM && CPT <= 8 && Cell<E>::kBytes == 16;
+
 // Fit one problem (f) with a team of CTAs.  The caller provides the
 // degenerate threshold and this CTA's shared memory; the ring must be set up
 // for f.N.  Writes V, U, W and lambda/iters for k < found; returns the
@@ -1703,7 +1766,10 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
     const int ring_ppr = two ? 1 : PPR;
     // reduced pass partials: this CTA's N-slice, then the k-vector (b' or the Gram row)
     float* rb = reinterpret_cast<float*>(dyn_smem + f.ring_bytes);
-    float* ka = rb + f.max_slice + f.ldk;
+    // with the two-reduction step rb also holds c' after b', and 3 ldk floats follow ka
+    const bool gs2 = kGs2Step<CPT, E, WARM, Team> && f.gs2 != 0;
+    float* ka = rb + f.max_slice + (gs2 ? 2 : 1) * f.ldk;
+    float* kx3 = ka + f.ldk;
     const int nc1 = n1 - n0;
     float* sv = rb;
     float* kb = rb + nc1;
@@ -1717,15 +1783,28 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
     float* Vl = f.V;
     float* Ul = f.U;
     float* Wl = f.W;
+    // Two-reduction GS step (f.gs2): this CTA's rows of Q and the matrices Z and
+    // GV = V^T V, column-major with leading dimension ldk (element (i, j) at j ldk + i).
+    float* Ql = nullptr;
+    float* Zs = nullptr;
+    float* GVs = nullptr;
     if (f.res_rows > 0) {
         float* rbase = reinterpret_cast<float*>(dyn_smem + f.res_off);
-        const int nres = f.res_rows * f.ldv + f.max_slice * (f.ldu + f.ldw);
+        const int nres = f.res_rows * f.ldv + f.max_slice * (f.ldu + f.ldw) +
+                         (gs2 ? f.res_rows * f.ldv + 2 * f.ldk * f.ldk : 0);
         for (int i = tid; i < nres; i += T) rbase[i] = 0.f;
         Vl = rbase - (size_t)r0 * f.ldv;
         Ul = rbase + (size_t)f.res_rows * f.ldv - (size_t)n0 * f.ldu;
         Wl = rbase + (size_t)f.res_rows * f.ldv + (size_t)f.max_slice * f.ldu - (size_t)n0 * f.ldw;
+        if (gs2) {
+            float* qbase = rbase + (size_t)f.res_rows * f.ldv + (size_t)f.max_slice * (f.ldu + f.ldw);
+            Ql = qbase - (size_t)r0 * f.ldv;
+            Zs = qbase + (size_t)f.res_rows * f.ldv;
+            GVs = Zs + (size_t)f.ldk * f.ldk;
+        }
         __syncthreads();
     }
+    double lam0 = 0.0;  // lambda of component 0 (the two-reduction step's range guard)
 
     int status = kStOK, found = K;
     long long total = 0;
@@ -1749,6 +1828,8 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
         // ------------- start: deflate component k-1 inside the pass that takes R(k)
         __syncthreads();
         PHASE_MARK(0);
+        if (gs2 && k > 1)  // a' of component k-1's last iteration: Z(i, k-1) before its h term
+            for (int i = tid; i < k - 1; i += T) Zs[(size_t)(k - 1) * f.ldk + i] = vinv_prev * ka[i];
         const bool defl = k > 0;
         const float lamf = gs ? (float)lam_prev : 1.f;
         // learned warm start (the WARM instantiations only): features, network output, and a
@@ -1885,6 +1966,19 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                 for (int j = tid; j < k; j += T) kb[j] = (float)ldcg(f.red + j);
                 __syncthreads();
             }
+            if (gs2) {
+                // this CTA's slice of U_(k)^T u_{k-1} (h, ending with u_{k-1}.u_{k-1}),
+                // W^T u_{k-1} (r) and u_{k-1}.u_pre (s1) of component k-1's last iteration,
+                // taken before W and u_pre change: pB[k, 3k)
+                const int km = k - 1;
+                auto uk = [&](int n) { return Ul[(size_t)n * f.ldu + km]; };
+                rows_times_matrix(Ul, f.ldu, n0, n1, k, uk, pB + k, sm);
+                if (km > 0) rows_times_matrix(Wl, f.ldw, n0, n1, km, uk, pB + 2 * k, sm);
+                ff su = ff_zero();
+                for (int n = n0 + tid; n < n1; n += T) su = ff_add(su, ff_mul_ff(uk(n), ldcg(f.upre + n)));
+                su = block_sum_ff(su, sm);
+                if (tid == 0) pB[3 * k - 1] = __fadd_rn(su.hi, su.lo);
+            }
             {
                 const int km = k - 1;
                 const float lpf = (float)lam_prev;
@@ -1904,7 +1998,37 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
             __syncthreads();
             rows_times_matrix(Ul, f.ldu, n0, n1, k, [&](int n) { return sv[n - n0]; }, pB, sm);
             GS_SYNC();
-            if (small_k) {
+            if (small_k && gs2) {
+                gather_reduce(f, sm, G, 0, 0, 0, f.partB, f.LB, 3 * k, ident, kx3);
+                for (int j = tid; j < k; j += T) ka[j] = kx3[j];
+                // Keep Z = U^T W, GV = V^T V and Q = R_k U_(k) for the deflation of component
+                // k-1 (the same rank-1 algebra as W): kb holds the Gram row v_{k-1}.v_j
+                const int km = k - 1;
+                const float lpf = (float)lam_prev;
+                const float* h = kx3 + k;
+                const float* rr = kx3 + 2 * k;
+                const float s1 = kx3[3 * k - 1], s2 = kx3[k + km];
+                for (int e = tid; e < k * k; e += T) {
+                    const int i = e / k, j = e % k;
+                    float* z = Zs + (size_t)j * f.ldk + i;
+                    if (i < km && j < km)
+                        *z = fmaf(-lpf * h[i], kb[j], *z);
+                    else if (i < km)  // j = k-1: vinv a'_i was stored at the start
+                        *z = fmaf(-lpf * h[i], kb[km], *z);
+                    else if (j < km)  // i = k-1
+                        *z = fmaf(-lpf * s2, kb[j], rr[j]);
+                    else
+                        *z = fmaf(-lpf * s2, kb[km], vinv_prev * s1);
+                    if (i == km || j == km) GVs[(size_t)j * f.ldk + i] = kb[i == km ? j : i];
+                }
+                for (int e = tid; e < (r1 - r0) * k; e += T) {
+                    const int r = r0 + e / k, i = e % k;
+                    const float vk = lpf * Vl[(size_t)r * f.ldv + km];
+                    float* q = Ql + (size_t)r * f.ldv + i;
+                    *q = (i < km) ? fmaf(-vk, h[i], *q) : fmaf(-vk, s2, ldcg(f.vraw + r) * inv_nu);
+                }
+                __syncthreads();
+            } else if (small_k) {
                 gather_reduce(f, sm, G, 0, 0, 0, f.partB, f.LB, k, ident, ka);
             } else {
                 reduce_cols_distributed(f.partB, G, g, f.LB, 0, k, f.red);
@@ -1994,7 +2118,13 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                 sc = ff{__int_as_float(0x7fc00000), 0.f};
             }
             write_scalar(f, g, 0, sc);
-            if (gs && k > 0)  // b' = V_(k)^T v' over this CTA's rows
+            // The two-reduction step is tried once the spectrum seen so far spans at most 64x
+            // (lambda_0 <= 64 mu): there Q and Z track R_k U and U^T W to the accuracy of the
+            // direct products.  Every CTA decides alike from the same reduced values.
+            const bool try2 = gs2 && gs && k > 0 && mu.hi > 0.f && (float)lam0 <= 64.f * mu.hi;
+            if (try2)  // b' = V_(k)^T v' and c' = Q^T v' = U^T s' over this CTA's rows
+                rows_times_two(Vl, Ql, f.ldv, r0, r1, k, [&](int r) { return f.vraw[r]; }, pA + N, pA + N + k, sm);
+            else if (gs && k > 0)  // b' = V_(k)^T v' over this CTA's rows
                 rows_times_matrix(Vl, f.ldv, r0, r1, k, [&](int r) { return f.vraw[r]; }, pA + N, sm);
             PHASE_MARK(3);
             GS_SYNC();
@@ -2003,8 +2133,11 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
             ++total;
             const bool small_k = k <= f.redundant_max;
             // sff[0] = ||u'||^2 (pass input), sff[1] = ||v'||^2; this CTA's slice of s' (+ b')
-            gather_reduce(f, sm, G, 2, 2 + buf, 0, f.partA, f.LA, nc1 + ((gs && k > 0 && small_k) ? k : 0),
-                          slice_then_k, rb);
+            if (try2)  // the slice, b' and c': up to 128 values per round trip
+                gather_reduce<4>(f, sm, G, 2, 2 + buf, 0, f.partA, f.LA, nc1 + 2 * k, slice_then_k, rb);
+            else
+                gather_reduce(f, sm, G, 2, 2 + buf, 0, f.partA, f.LA, nc1 + ((gs && k > 0 && small_k) ? k : 0),
+                              slice_then_k, rb);
             const ff nu2 = sm.sff[0];
             const ff nvp = sm.sff[1];
             const float nu2f = __fadd_rn(nu2.hi, nu2.lo);
@@ -2016,6 +2149,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
             inv_nu = __fdiv_rn(1.f, __fsqrt_rn(nu2f));
             ff lam2p;  // ||v' - V b'||^2 in pass scale
             const int nbuf = buf ^ 1;
+            bool step2 = false;  // this iteration took the two-reduction GS step
             if (!gs || k == 0) {
                 lam2p = nvp;
                 PHASE_MARK(6);
@@ -2029,31 +2163,67 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                     __syncthreads();
                 }
                 PHASE_MARK(6);
-                ff l2 = ff_zero();
-                matrix_times_vector(
-                    Vl, f.ldv, r0, r1, k, kb, [&](int r) { return ldcg(f.vraw + r); },
-                    [&](int r, float s, float p) {
-                        const float vc = p - s;
-                        f.vcorr[r] = vc;
-                        l2 = ff_add(l2, ff_sqr(vc));
-                    });
-                matrix_times_vector(
-                    Wl, f.ldw, n0, n1, k, kb, [&](int n) { return sv[n - n0]; },
-                    [&](int n, float s, float p) { f.upre[n] = p - s; });
-                __syncthreads();
-                rows_times_matrix(Ul, f.ldu, n0, n1, k, [&](int n) { return f.upre[n]; }, pB, sm);
-                l2 = block_sum_ff(l2, sm);
-                write_scalar(f, g, 1, l2);
-                PHASE_MARK(7);
-                GS_SYNC();
-                PHASE_MARK(8);
-                gather_reduce(f, sm, G, 1, 1, 0, f.partB, f.LB, small_k ? k : 0, ident, ka);
-                lam2p = sm.sff[0];
-                if (!small_k) {
-                    reduce_cols_distributed(f.partB, G, g, f.LB, 0, k, f.red);
-                    GS_SYNC();
-                    for (int jj = tid; jj < k; jj += T) ka[jj] = (float)ldcg(f.red + jj);
+                if (try2) {
+                    // a' = U^T (s' - W b') = c' - Z b' and ||v' - V b'||^2 = ||v'||^2 - 2 b'.b' +
+                    // b'^T (V^T V) b' from reduced values only (one warp, fixed order); taken when
+                    // the subtraction loses little (b'.b' <= ||v'||^2 / 4).
+                    if (warp == 0) {
+                        const float* kc = kb + k;
+                        ff bb = ff_zero(), bg = ff_zero();
+                        for (int i = lane; i < k; i += 32) {
+                            float t = 0.f, z = 0.f;
+                            for (int jj = 0; jj < k; ++jj) {
+                                const float bj = kb[jj];
+                                t = fmaf(GVs[(size_t)jj * f.ldk + i], bj, t);
+                                z = fmaf(Zs[(size_t)jj * f.ldk + i], bj, z);
+                            }
+                            ka[i] = kc[i] - z;
+                            bb = ff_add(bb, ff_sqr(kb[i]));
+                            bg = ff_add(bg, ff_mul_ff(kb[i], t));
+                        }
+                        bb = warp_sum_ff(bb);
+                        bg = warp_sum_ff(bg);
+                        if (lane == 0) {
+                            sm.lam2s = ff_add(nvp, ff_add(bg, ff_neg(ff_add(bb, bb))));
+                            sm.step2 = 4.f * (bb.hi + bb.lo) <= nvp.hi + nvp.lo;
+                        }
+                    }
                     __syncthreads();
+                    step2 = sm.step2 != 0;
+                }
+                if (step2) {
+                    lam2p = sm.lam2s;
+                    matrix_times_vector(
+                        Wl, f.ldw, n0, n1, k, kb, [&](int n) { return sv[n - n0]; },
+                        [&](int n, float s, float p) { f.upre[n] = p - s; });
+                    __syncthreads();
+                } else {
+                    ff l2 = ff_zero();
+                    matrix_times_vector(
+                        Vl, f.ldv, r0, r1, k, kb, [&](int r) { return ldcg(f.vraw + r); },
+                        [&](int r, float s, float p) {
+                            const float vc = p - s;
+                            f.vcorr[r] = vc;
+                            l2 = ff_add(l2, ff_sqr(vc));
+                        });
+                    matrix_times_vector(
+                        Wl, f.ldw, n0, n1, k, kb, [&](int n) { return sv[n - n0]; },
+                        [&](int n, float s, float p) { f.upre[n] = p - s; });
+                    __syncthreads();
+                    rows_times_matrix(Ul, f.ldu, n0, n1, k, [&](int n) { return f.upre[n]; }, pB, sm);
+                    l2 = block_sum_ff(l2, sm);
+                    write_scalar(f, g, 1, l2);
+                    PHASE_MARK(7);
+                    GS_SYNC();
+                    PHASE_MARK(8);
+                    gather_reduce(f, sm, G, 1, 1, 0, f.partB, f.LB, small_k ? k : 0, ident, ka);
+                    lam2p = sm.sff[0];
+                    if (!small_k) {
+                        reduce_cols_distributed(f.partB, G, g, f.LB, 0, k, f.red);
+                        GS_SYNC();
+                        for (int jj = tid; jj < k; jj += T) ka[jj] = (float)ldcg(f.red + jj);
+                        __syncthreads();
+                    }
                 }
                 PHASE_MARK(10);
             }
@@ -2104,6 +2274,12 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
             if (stop) {
                 if (stop == 3 && status == kStOK) status = kStNotConverged;
                 // finalize component k: V(k), U(k), lambda_k, iters_k
+                if (step2) {  // v' - V b' for this CTA's rows (the two-reduction step skipped it)
+                    matrix_times_vector(
+                        Vl, f.ldv, r0, r1, k, kb, [&](int r) { return ldcg(f.vraw + r); },
+                        [&](int r, float s, float p) { f.vcorr[r] = p - s; });
+                    __syncthreads();
+                }
                 const float vinv = __fdiv_rn(1.f, __fsqrt_rn(l2f));
                 const bool res = f.res_rows > 0;
                 for (int r = r0 + tid; r < r1; r += T) {
@@ -2117,6 +2293,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                     if (res) Ul[(size_t)n * f.ldu + k] = u;
                 }
                 lam_prev = ff_to_double(lamff);
+                if (k == 0) lam0 = lam_prev;
                 if (g == 0 && tid == 0) {
                     f.lam[k] = lam_prev;
                     f.iters[k] = j;

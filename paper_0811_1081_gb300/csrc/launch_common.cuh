@@ -24,16 +24,23 @@ struct Plan {
     size_t res;     // their bytes
     int cb;     // bytes of one cell of R: 16 (FP32 storage) or 8 (bfloat16 storage)
     bool warm;  // the kernel with the learned warm start
+    int gs2;    // GS-PCA iterations may take the two-reduction step (see FitArgs::gs2)
     size_t dyn;
 };
 
 // Largest resident factor block chosen automatically.
 constexpr size_t kResMaxBytes = 48 * 1024;
+// The two-reduction GS step: up to this many components, and a resident block
+// (with Q rows and the matrices Z and V^T V) of at most this size.
+constexpr int kGs2MaxK = 64;
+constexpr size_t kResGs2MaxBytes = 96 * 1024;
 
 // Shared memory after the ring: the CTA's slice of the pass result, two
-// k-vectors, and the slice of the learned start's second pass result.
-inline size_t vec_bytes(int ldk, int max_slice) {
-    return (sizeof(float) * (2 * (size_t)ldk + 2 * (size_t)max_slice) + 15) / 16 * 16;
+// k-vectors, and the slice of the learned start's second pass result.  With the
+// two-reduction GS step: the slice, b' and c' (max_slice + 2 ldk), a' (ldk) and
+// the component-start products (3 ldk).
+inline size_t vec_bytes(int ldk, int max_slice, int gs2) {
+    return (sizeof(float) * ((gs2 ? 6 : 2) * (size_t)ldk + 2 * (size_t)max_slice) + 15) / 16 * 16;
 }
 
 // Bytes of one cell of R (4 rows x 1 column) for a storage type.
@@ -108,7 +115,6 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
     p->G = G;
     p->ldk = ws_ld(K);
     p->max_slice = (N + G - 1) / G + 1;
-    const size_t vec = vec_bytes(p->ldk, p->max_slice);
     // GS-PCA: keep this CTA's rows of V and slices of U and W in shared memory when
     // they take at most kResMaxBytes (auto) or when asked to (opts->resident = 1)
     const int np_cta = (np + G - 1) / G;
@@ -116,10 +122,23 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
     const int rmode = opts ? opts->resident : 0;
     p->res_rows = 0;
     p->res = 0;
+    p->gs2 = 0;
     if (gs && rmode != 2 && (rmode == 1 || res <= kResMaxBytes)) {
         p->res_rows = 4 * np_cta;
         p->res = res;
+        // the two-reduction GS step adds this CTA's rows of Q and the two ldk x ldk
+        // matrices; FP32 storage only (Q tracks R U through the deflations without their
+        // rounding, which bfloat16 storage makes far larger than the step's own), up to
+        // 4096 columns (wider rows are dominated by the pass over R)
+        const size_t extra = sizeof(float) * ((size_t)4 * np_cta * ldf + 2 * (size_t)p->ldk * p->ldk);
+        if (!p->warm && cb == 16 && p->cpt <= 8 && (!opts || opts->gs_step == 0) && K <= kGs2MaxK &&
+            K <= kRedundantMax &&
+            res + extra <= kResGs2MaxBytes) {
+            p->gs2 = 1;
+            p->res = res + extra;
+        }
     }
+    const size_t vec = vec_bytes(p->ldk, p->max_slice, p->gs2);
     int optin = 0;
     cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (e != cudaSuccess) return e;
@@ -222,7 +241,8 @@ inline FitArgs make_args(const Workspace& w, const Plan& p, int M, int N, int K,
     a.timing = nullptr;
     a.tma_stages = p.S;
     a.dot_groups = p.groups;
-    a.ring_bytes = (int)(p.dyn - vec_bytes(p.ldk, p.max_slice) - p.res);
+    a.ring_bytes = (int)(p.dyn - vec_bytes(p.ldk, p.max_slice, p.gs2) - p.res);
+    a.gs2 = p.gs2;
     a.res_rows = p.res_rows;
     a.res_off = (int)(p.dyn - p.res);  // after the ring and the vectors
     a.ldk = p.ldk;

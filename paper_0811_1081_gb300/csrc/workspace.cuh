@@ -27,7 +27,8 @@ inline int ws_ld(int K) {
     while (ld < K) ld *= 2;
     return ld;
 }
-inline int ws_LA(int N, int K) { return (int)align_up((size_t)N + K + 4, 4); }
+// Pass partials: s' (N), b' and c' (K each), 4 spare.
+inline int ws_LA(int N, int K) { return (int)align_up((size_t)N + 2 * (size_t)K + 4, 4); }
 inline int ws_xcap(long Mp, int N) { return (int)(((N + 31) / 32) * ((Mp / 4 + 31) / 32)); }
 
 struct Workspace {
@@ -46,7 +47,7 @@ inline Workspace carve(void* base, const WsDims& d) {
     Workspace w{};
     w.ld = ws_ld(d.K);
     w.LA = ws_LA(d.N, d.K);
-    w.LB = w.ld;
+    w.LB = 3 * w.ld;  // a' (GS step), or a, U^T u, W^T u and u.u_pre (component start)
     w.G = d.G;
     w.xcap = ws_xcap(d.Mp, d.N);
     char* b = static_cast<char*>(base);

@@ -283,7 +283,8 @@ def test_load_path_gives_the_same_fit(gp, shape, storage):
 @pytest.mark.parametrize("shape", [(1003, 517, 6), (10000, 2000, 4), (64, 4097, 3)])
 def test_resident_factors_do_not_change_results(gp, shape):
     """Keeping the factor rows/slices in shared memory or in global memory is a placement
-    choice only: the two fits are bit-identical."""
+    choice only: with the same Gram-Schmidt step (the three-reduction one, which both
+    placements have) the two fits are bit-identical."""
     import torch
 
     M, N, K = shape
@@ -292,8 +293,36 @@ def test_resident_factors_do_not_change_results(gp, shape):
     outs = []
     with gp.Handle(M, N, K) as h:
         for mode in (1, 2):
-            r = h.fit(Xd, K, tol=1e-6, max_iter=1000, algo="gs", want_R=True, resident=mode)
+            r = h.fit(Xd, K, tol=1e-6, max_iter=1000, algo="gs", want_R=True, resident=mode, gs_step=1)
             torch.cuda.synchronize()
             outs.append([t.cpu().numpy() for t in (r.T, r.P, r.lam, r.iters, r.R)])
     for a, b in zip(*outs):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("shape", [(1003, 517, 6), (10000, 2000, 12), (700, 2000, 40), (64, 4097, 3), (5000, 300, 64)])
+def test_two_reduction_gs_step_matches_three(gp, shape):
+    """The Gram-Schmidt step from maintained Q = R U, Z = U^T W and V^T V (two grid-wide
+    reductions per iteration) against the three-reduction step of Sec. 2.3: the same fit to
+    FP32 rounding (the second run replays the first's iteration counts), and GS-PCA's
+    orthogonality kept.  The planted spectrum decays by 0.85 per component, so the larger K
+    also crosses the 64x range beyond which the step falls back to three reductions."""
+    import torch
+
+    M, N, K = shape
+    X32 = synth.planted(M, N, 5.0, 0.85, 0.01, (43, M, N)).X.astype(np.float32)
+    Xd = torch.from_numpy(X32).cuda()
+    with gp.Handle(M, N, K) as h:
+        a = h.fit(Xd, K, tol=1e-6, max_iter=1000, algo="gs", gs_step=1)
+        lock = [int(v) for v in a.iters.cpu().numpy()]
+        b = h.fit(Xd, K, tol=1e-6, max_iter=1000, algo="gs", gs_step=0, iters_lock=lock)
+        torch.cuda.synchronize()
+        la, lb = a.lam.cpu().numpy(), b.lam.cpu().numpy()
+        Pa, Pb = a.P.cpu().numpy().astype(np.float64), b.P.cpu().numpy().astype(np.float64)
+        Ta, Tb = a.T.cpu().numpy().astype(np.float64), b.T.cpu().numpy().astype(np.float64)
+    assert a.status == 0 and b.status == 0
+    assert np.all(np.abs(la - lb) <= 1e-5 * la)
+    for k in range(K):
+        assert angle(Pa[:, k], Pb[:, k]) <= 1e-4
+        assert angle(Ta[:, k], Tb[:, k]) <= 1e-4
+    assert np.abs(Pb.T @ Pb - np.eye(K)).max() <= ORTHO

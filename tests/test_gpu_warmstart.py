@@ -168,13 +168,13 @@ def test_fit_with_learned_start_locked(gp, shape):
 
 def test_zero_network_is_the_papers_fit_bit_for_bit(gp):
     """With w == 0 the warm-start machinery runs but never offers a candidate: the fit is
-    bit-identical to the plain one."""
+    bit-identical to the plain one (with the same, three-reduction Gram-Schmidt step)."""
     import torch
 
     X32 = synth.planted(600, 250, 10.0, 0.85, 0.01, 79).X.astype(np.float32)
     g = run_warm(gp, X32, 6, np.zeros(oracle.ws_nparams(), np.float32), sketch(600))
     with gp.Handle(600, 250, 6) as h:
-        r = h.fit(torch.from_numpy(X32).cuda(), 6, algo="gs", want_R=True)
+        r = h.fit(torch.from_numpy(X32).cuda(), 6, algo="gs", want_R=True, gs_step=1)
         torch.cuda.synchronize()
         assert not g["choice"].any()
         assert np.array_equal(g["P"], r.P.cpu().numpy().astype(np.float64))
