@@ -1079,6 +1079,43 @@ __device__ __forceinline__ void matrix_times_vector(const float* A, int lda, int
     }
 }
 
+// For every row r in [r0, r1): fn(r, A_r . x, B_r . y, pre(r)) with kk <= 64
+// columns and x, y in shared memory; each product in the order of the general
+// path of matrix_times_vector.
+template <class Pre, class Fn>
+__device__ __forceinline__ void matrix_times_two(const float* A, const float* B, int lda, int r0, int r1, int kk,
+                                                 const float* x, const float* y, Pre pre, Fn fn) {
+    constexpr int MAXR = 8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bool c0 = lane < kk, c1 = lane + 32 < kk;
+    const float x0 = c0 ? x[lane] : 0.f, x1 = c1 ? x[lane + 32] : 0.f;
+    const float y0 = c0 ? y[lane] : 0.f, y1 = c1 ? y[lane + 32] : 0.f;
+    for (int rb = r0 + warp; rb < r1; rb += nw * MAXR) {
+        float accA[MAXR], accB[MAXR], pv[MAXR];
+#pragma unroll
+        for (int i = 0; i < MAXR; ++i) {
+            const int r = rb + nw * i;
+            const bool ok = r < r1;
+            pv[i] = ok ? pre(r) : 0.f;
+            const float* ar = A + (size_t)r * lda;
+            const float* br = B + (size_t)r * lda;
+            const float a0 = (ok && c0) ? ar[lane] : 0.f, a1 = (ok && c1) ? ar[lane + 32] : 0.f;
+            const float b0 = (ok && c0) ? br[lane] : 0.f, b1 = (ok && c1) ? br[lane + 32] : 0.f;
+            accA[i] = fmaf(a1, x1, fmaf(a0, x0, 0.f));
+            accB[i] = fmaf(b1, y1, fmaf(b0, y0, 0.f));
+        }
+        const float sA = warp_multi_reduce<MAXR>(accA, lane);  // lane l: row index l >> 2
+        const float sB = warp_multi_reduce<MAXR>(accB, lane);
+        const int i = lane >> 2;
+        float p = pv[0];
+#pragma unroll
+        for (int t = 1; t < MAXR; ++t)
+            if (t == i) p = pv[t];
+        const int r = rb + nw * i;
+        if ((lane & 3) == 0 && r < r1) fn(r, sA, sB, p);
+    }
+}
+
 // CTA-wide float-float sum (deterministic: warp butterflies, then a 16-lane
 // butterfly over the warp sums), result in every thread.
 __device__ __forceinline__ ff block_sum_ff(ff v, SmemFit& sm) {
@@ -1972,8 +2009,8 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                 // taken before W and u_pre change: pB[k, 3k)
                 const int km = k - 1;
                 auto uk = [&](int n) { return Ul[(size_t)n * f.ldu + km]; };
-                rows_times_matrix(Ul, f.ldu, n0, n1, k, uk, pB + k, sm);
-                if (km > 0) rows_times_matrix(Wl, f.ldw, n0, n1, km, uk, pB + 2 * k, sm);
+                // (W's column k-1, not yet formed, lands in pB[3k-1] and is replaced by s1)
+                rows_times_two(Ul, Wl, f.ldu, n0, n1, k, uk, pB + k, pB + 2 * k, sm);
                 ff su = ff_zero();
                 for (int n = n0 + tid; n < n1; n += T) su = ff_add(su, ff_mul_ff(uk(n), ldcg(f.upre + n)));
                 su = block_sum_ff(su, sm);
@@ -1999,7 +2036,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
             rows_times_matrix(Ul, f.ldu, n0, n1, k, [&](int n) { return sv[n - n0]; }, pB, sm);
             GS_SYNC();
             if (small_k && gs2) {
-                gather_reduce(f, sm, G, 0, 0, 0, f.partB, f.LB, 3 * k, ident, kx3);
+                gather_reduce<4>(f, sm, G, 0, 0, 0, f.partB, f.LB, 3 * k, ident, kx3);
                 for (int j = tid; j < k; j += T) ka[j] = kx3[j];
                 // Keep Z = U^T W, GV = V^T V and Q = R_k U_(k) for the deflation of component
                 // k-1 (the same rank-1 algebra as W): kb holds the Gram row v_{k-1}.v_j
@@ -2192,11 +2229,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                     step2 = sm.step2 != 0;
                 }
                 if (step2) {
-                    lam2p = sm.lam2s;
-                    matrix_times_vector(
-                        Wl, f.ldw, n0, n1, k, kb, [&](int n) { return sv[n - n0]; },
-                        [&](int n, float s, float p) { f.upre[n] = p - s; });
-                    __syncthreads();
+                    lam2p = sm.lam2s;  // s' - W b' is formed with the next loading below
                 } else {
                     ff l2 = ff_zero();
                     matrix_times_vector(
@@ -2254,6 +2287,17 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                     nq2 = ff_add(nq2, ff_sqr(un));
                     if (gs) f.upre[n] = sv[n - n0];
                 }
+            } else if (step2) {
+                // u_pre = s' - W b' and the next loading (u_pre - U a') nscale in one sweep
+                matrix_times_two(
+                    Wl, Ul, f.ldw, n0, n1, k, kb, ka, [&](int n) { return sv[n - n0]; },
+                    [&](int n, float sw, float su, float s0) {
+                        const float up = s0 - sw;
+                        f.upre[n] = up;
+                        const float un = (up - su) * nscale;
+                        f.ut[(size_t)nbuf * N + n] = un;
+                        nq2 = ff_add(nq2, ff_sqr(un));
+                    });
             } else {
                 matrix_times_vector(
                     Ul, f.ldu, n0, n1, k, ka, [&](int n) { return ldcg(f.upre + n); },
