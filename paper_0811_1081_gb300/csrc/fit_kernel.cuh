@@ -2208,12 +2208,21 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                         const float* kc = kb + k;
                         ff bb = ff_zero(), bg = ff_zero();
                         for (int i = lane; i < k; i += 32) {
-                            float t = 0.f, z = 0.f;
-                            for (int jj = 0; jj < k; ++jj) {
-                                const float bj = kb[jj];
-                                t = fmaf(GVs[(size_t)jj * f.ldk + i], bj, t);
-                                z = fmaf(Zs[(size_t)jj * f.ldk + i], bj, z);
+                            // even and odd j in separate chains (twice the independent FMAs)
+                            float t0 = 0.f, t1 = 0.f, z0 = 0.f, z1 = 0.f;
+                            int jj = 0;
+                            for (; jj + 1 < k; jj += 2) {
+                                const float b0 = kb[jj], b1 = kb[jj + 1];
+                                t0 = fmaf(GVs[(size_t)jj * f.ldk + i], b0, t0);
+                                z0 = fmaf(Zs[(size_t)jj * f.ldk + i], b0, z0);
+                                t1 = fmaf(GVs[(size_t)(jj + 1) * f.ldk + i], b1, t1);
+                                z1 = fmaf(Zs[(size_t)(jj + 1) * f.ldk + i], b1, z1);
                             }
+                            if (jj < k) {
+                                t0 = fmaf(GVs[(size_t)jj * f.ldk + i], kb[jj], t0);
+                                z0 = fmaf(Zs[(size_t)jj * f.ldk + i], kb[jj], z0);
+                            }
+                            const float t = t0 + t1, z = z0 + z1;
                             ka[i] = kc[i] - z;
                             bb = ff_add(bb, ff_sqr(kb[i]));
                             bg = ff_add(bg, ff_mul_ff(kb[i], t));
