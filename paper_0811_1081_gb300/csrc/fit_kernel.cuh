@@ -23,10 +23,15 @@
 // barrier that precedes it.
 //
 // Barriers per iteration: NIPALS and GS component 0 need two (after the
-// pass; after the new loading); GS components k > 0 need three (one more
-// after u_pre' = s' - W b' and its coefficients a' = U^T u_pre').  The
-// k-vectors b' and a' are reduced by every CTA from the CTA partials when G*k
-// is small, otherwise once across the grid with one more barrier each.
+// pass; after the new loading); GS components k > 0 need three in the form of
+// Sec. 2.3 (one more after u_pre' = s' - W b' and its coefficients
+// a' = U^T u_pre').  With FP32 storage, up to 64 components and 4096 columns
+// per CTA the middle one goes: Q = R_k U and Z = U^T W are kept up to date per
+// component like W, so a' = Q^T v' - Z b' (Q^T v' reduced with b' after the
+// pass) and ||v' - V b'||^2 = ||v'||^2 - 2 b'.b' + b'^T V^T V b' come from
+// reduced values, where that is numerically safe (see the guards at the step).
+// The k-vectors are reduced by every CTA from the CTA partials when G*k is
+// small, otherwise once across the grid with one more barrier each.
 //
 // Precision: R and every O(M N), O(M k), O(N k) product are FP32 with FP32
 // sums inside a CTA; cross-CTA vector sums are FP32 over the CTA partials of
@@ -89,7 +94,8 @@ struct FitArgs {
     int res_rows;             // > 0: this CTA's rows of V (res_rows) and its slices of U and W
                               // (max_slice each) live in shared memory at byte res_off
     int res_off;
-    int gs2;                  // 1 (single-problem GS-PCA, FP32 storage, resident, K <= 64): the
+    int gs2;                  // 1 (single-problem GS-PCA, FP32 storage, resident, K <= 64, up to
+                              // 4096 columns per CTA): the
                               // resident block also holds this CTA's rows of Q = R_k U_(k) and the
                               // matrices Z = U^T W and V^T V (ldk x ldk), kept up to date per component, and an
                               // iteration may form a' and ||v' - V b'||^2 from them (two grid-wide
