@@ -100,3 +100,38 @@ def test_ctypes_structs_match_header(cname, pyname):
     want = header_struct_fields(cname)
     got = [f.rstrip("_") for f, _ in getattr(gp, pyname)._fields_]
     assert got == want, (cname, got, want)
+
+
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a header struct, from a C program compiled with gcc."""
+    import shutil
+    import subprocess
+    import tempfile
+
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "gspca.h"', "int main(void) {",
+             f'  printf("%zu\\n", sizeof({struct}));']
+    lines += [f'  printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines) + "\n")
+        subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(v) for v in out[1:]]
+
+
+@pytest.mark.parametrize("struct,pyname,rename", [("gspca_opts", "Opts", {}), ("gspca_info", "Info", {}),
+                                                  ("gspca_problem", "Problem", {"lambda_": "lambda"}),
+                                                  ("gspca_warm_start", "WarmStartC", {})])
+def test_binding_structs_match_the_header_layout(struct, pyname, rename):
+    """The ctypes mirrors of the ABI structs have the header's size, field order and offsets."""
+    import paper_0811_1081_gb300 as gp
+
+    cls = getattr(gp, pyname)
+    names = [rename.get(n, n) for n, _ in cls._fields_]
+    size, offs = _c_layout(struct, names)
+    assert ctypes.sizeof(cls) == size
+    assert [getattr(cls, n).offset for n, _ in cls._fields_] == offs
