@@ -147,3 +147,86 @@ def test_component_start_updates_are_exact_for_any_factors():
         np.testing.assert_allclose(Q.T @ vp - Z @ b, U.T @ (R.T @ vp - W @ b), atol=1e-10 * np.abs(Q.T @ vp).max())
         lhs = vp @ vp - 2 * b @ b + b @ G @ b
         assert abs(lhs - np.sum((vp - V @ b) ** 2)) <= 1e-10 * (vp @ vp + b @ G @ b)
+
+
+def _fp32_run(X, K, tol, ratio_guard):
+    """GS-PCA in FP32 (numpy) with the two-reduction step as the kernel takes it:
+    Q, Z, GV maintained through the deflations (which round in FP32 and are not
+    tracked), the step taken when b'.b' <= ||v'||^2 / 4 and lambda_0 <= guard mu."""
+    f32 = np.float32
+    R = X.astype(f32)
+    M, N = R.shape
+    V = np.zeros((M, K), f32); U = np.zeros((N, K), f32); W = np.zeros((N, K), f32)
+    Q = np.zeros((M, K), f32); Z = np.zeros((K, K), f32); G = np.zeros((K, K), f32)
+    lams, a_last = [], np.zeros(K, f32)
+    vinv_prev = inv_nu = f32(0)
+    vraw_last = upre_last = None
+    for k in range(K):
+        if k > 0:
+            km, lam = k - 1, f32(lams[-1])
+            v, u = V[:, km], U[:, km]
+            g = V[:, :k].T @ v
+            h = U[:, :k].T @ u
+            r = W[:, :km].T @ u
+            s1, s2 = f32(u @ upre_last), h[km]
+            Zn = np.zeros((K, K), f32)
+            Zn[:km, :km] = Z[:km, :km] - lam * np.outer(h[:km], g[:km])
+            Zn[:km, km] = vinv_prev * a_last[:km] - lam * h[:km] * g[km]
+            Zn[km, :km] = r - lam * s2 * g[:km]
+            Zn[km, km] = vinv_prev * s1 - lam * s2 * g[km]
+            Z = Zn
+            G[km, :k] = g
+            G[:k, km] = g
+            Q[:, :km] -= lam * np.outer(v, h[:km])
+            Q[:, km] = vraw_last * inv_nu - lam * v * s2
+            W[:, :km] -= lam * np.outer(u, g[:km])
+            W[:, km] = upre_last * vinv_prev - lam * u * g[km]
+            R = (R - lam * np.outer(v, u)).astype(f32)
+        x = R[:, k].copy()
+        s0 = R.T @ x
+        a = U[:, :k].T @ s0
+        ut = ((s0 - U[:, :k] @ a) / (x @ x)).astype(f32)
+        mu = 0.0
+        for j in range(5000):
+            nu2 = float(ut @ ut)
+            vp = R @ ut
+            sp = R.T @ vp
+            b = V[:, :k].T @ vp
+            up = sp - W[:, :k] @ b
+            bb, vv = float(b @ b), float(vp @ vp)
+            vc = vp - V[:, :k] @ b
+            if k > 0 and mu > 0 and lams[0] <= ratio_guard * mu and 4 * bb <= vv:
+                a_ = Q[:, :k].T @ vp - Z[:k, :k] @ b
+                l2 = vv - 2 * bb + float(b @ G[:k, :k] @ b)
+            else:
+                a_ = U[:, :k].T @ up
+                l2 = float(vc @ vc)
+            lam = np.sqrt(l2 / nu2)
+            if abs(mu - lam) < tol * lam or j == 4999:
+                vinv_prev, inv_nu = f32(1 / np.sqrt(l2)), f32(1 / np.sqrt(nu2))
+                V[:, k], U[:, k] = vc * vinv_prev, ut * inv_nu
+                lams.append(lam)
+                vraw_last, upre_last = vp, up
+                a_last = np.zeros(K, f32)
+                a_last[:k] = a_
+                break
+            mu = lam
+            ut = ((up - U[:, :k] @ a_) * f32(np.sqrt(nu2) / l2)).astype(f32)
+    return np.array(lams), U
+
+
+def test_fp32_model_needs_the_range_guard():
+    """In FP32, Q and Z miss the rounding of each deflation; relative to lambda_k that error
+    grows with lambda_0 / lambda_k.  On a spectrum spanning ~5000x the step without the
+    range guard lets the loadings drift from orthogonality, with the kernel's guard
+    (lambda_0 <= 64 mu) they stay at FP32 rounding, and the singular values agree."""
+    X = synth.planted(800, 300, 10.0, 0.9, 0.0001, 9).X
+    K = 80
+    lam_g, U_g = _fp32_run(X, K, 1e-6, 64.0)
+    lam_n, U_n = _fp32_run(X, K, 1e-6, np.inf)
+    ortho_g = np.abs(U_g.T.astype(np.float64) @ U_g - np.eye(K)).max()
+    ortho_n = np.abs(U_n.T.astype(np.float64) @ U_n - np.eye(K)).max()
+    assert ortho_g <= 2e-6
+    assert ortho_n >= 4 * ortho_g
+    s = np.linalg.svd(X, compute_uv=False)
+    assert np.abs(lam_g - s[:K]).max() <= 1e-5 * s[0]
