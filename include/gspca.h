@@ -251,9 +251,10 @@ gspca_status gspca_fit_batched_async(gspca_t h, void *stream, const gspca_proble
  * library, which every GPU that loads the library holds until the process
  * exits.  The call runs on the current device and never calls cudaMalloc,
  * cudaFree or any allocating routine.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - Every call looks up the array's device address (cudaGetSymbolAddress)
+ *     with the current device, so the address stays right after a
+ *     cudaDeviceReset reloads the library's device code.  The first call on a
+ *     device also loads that code; make it before any stream capture.
  *   - Every call shares the one array and leaves its contents behind; the
  *     words that must start at zero (grid barrier, abort flag, status) are
  *     cleared by the call's own first kernel.  Calls whose work overlaps on

@@ -424,7 +424,8 @@ NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 def gspca_fit_noalloc(X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="gs", center: int = 0,
-                      iters_lock=None, want_R: bool = False, stream=None, check: bool = True) -> FitResult:
+                      iters_lock=None, want_R: bool = False, stream=None, check: bool = True,
+                      timeout_s: float = 0.0, test_stall: int = 0) -> FitResult:
     """gspca_fit without a handle and without any device allocation inside the library: the
     workspace is the library's fixed scratch array (NOALLOC_SCRATCH_BYTES per device).  For
     callers that must not allocate device memory.  Output tensors are the caller's (allocated
@@ -446,7 +447,7 @@ def gspca_fit_noalloc(X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="
     R = torch.empty((N, M), device=dev, dtype=torch.float32).t() if want_R else None
     if stream is None:
         stream = torch.cuda.current_stream(dev).cuda_stream
-    o, keep = _opts(center, iters_lock)
+    o, keep = _opts(center, iters_lock, timeout_s=timeout_s, test_stall=test_stall)
     with torch.cuda.device(dev):
         st = load().gspca_fit_noalloc(ctypes.c_void_p(stream), ctypes.c_void_p(X.data_ptr()), layout, int(ldx),
                                       M, N, int(K), float(tol), int(max_iter), _ALGOS[algo],

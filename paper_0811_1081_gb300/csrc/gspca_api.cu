@@ -47,14 +47,9 @@ gspca_status check_fit_args(gspca_t h, const void* X, gspca_layout layout, long 
     } else {
         return GSPCA_ERR_INVALID_ARG;
     }
+    const gspca_status ost = check_opts(opts, K);
+    if (ost != GSPCA_OK) return ost;
     if (opts) {
-        if (opts->center < 0 || opts->center > 2 || opts->grid_ctas < 0 || opts->timeout_s < 0 ||
-            opts->test_stall < 0 || opts->test_stall > 1 || opts->resident < 0 || opts->resident > 2 ||
-            opts->load_path < 0 || opts->load_path > 2 || opts->gs_step < 0 || opts->gs_step > 1)
-            return GSPCA_ERR_INVALID_ARG;
-        if (opts->iters_lock)
-            for (int k = 0; k < K; ++k)
-                if (opts->iters_lock[k] < 1) return GSPCA_ERR_INVALID_ARG;
         if (opts->warm) {
             const gspca_warm_start* w = opts->warm;
             if (!w->net || !w->G || w->G_rows < M) return GSPCA_ERR_INVALID_ARG;

@@ -52,6 +52,21 @@ inline int cpt_for(int N) {
     return c;
 }
 
+// Checks of the fields of gspca_opts shared by gspca_fit, gspca_fit_host and
+// gspca_fit_noalloc (the warm-start pointer is checked by each entry point,
+// since its support differs).  opts may be null.
+inline gspca_status check_opts(const gspca_opts* opts, int K) {
+    if (!opts) return GSPCA_OK;
+    if (opts->center < 0 || opts->center > 2 || opts->grid_ctas < 0 || !(opts->timeout_s >= 0) ||
+        opts->test_stall < 0 || opts->test_stall > 1 || opts->resident < 0 || opts->resident > 2 ||
+        opts->load_path < 0 || opts->load_path > 2 || opts->gs_step < 0 || opts->gs_step > 1)
+        return GSPCA_ERR_INVALID_ARG;
+    if (opts->iters_lock)
+        for (int k = 0; k < K; ++k)
+            if (opts->iters_lock[k] < 1) return GSPCA_ERR_INVALID_ARG;
+    return GSPCA_OK;
+}
+
 // Kernel attributes and launches per (columns per thread, storage type).  They
 // are defined beside the kernels (fit_inst.cuh) and instantiated once each in
 // the fit_*.cu translation units, so the host-side units compile no kernel.

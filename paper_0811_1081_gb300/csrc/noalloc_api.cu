@@ -1,13 +1,12 @@
 // gspca_fit_noalloc: the fit of gspca_fit for callers that must not allocate
-// device memory.  Its scratch workspace is one file-scope device array; the
-// host code below looks up that array's device address once per device and
-// lays the workspace of each call out inside it.  Nothing here calls
-// cudaMalloc, cudaFree or an allocating library routine.
+// device memory.  Its scratch workspace is one file-scope device array; every
+// call looks up that array's device address for the current device and lays
+// the workspace of the call out inside it.  Nothing here calls cudaMalloc,
+// cudaFree or an allocating library routine.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/gspca.h"
+#include "handle.h"
 #include "launch_common.cuh"
 
 using namespace gspca;
@@ -18,28 +17,19 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[GSPCA_NOALLOC_S
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-
-std::mutex g_setup_mu;
-void* g_scratch_addr[kMaxDevices];
-int g_num_sms[kMaxDevices];
-
-// Once per device, with that device current: resolve the array's device
-// address (checked) and the SM count.
+// With the caller's device current: the array's device address (checked) and
+// the SM count.  Resolved on every call rather than cached: after a
+// cudaDeviceReset (or any teardown of the primary context) the module is
+// loaded again and the array can sit at another address.
 gspca_status device_setup(int dev, void** addr, int* sms) {
-    if (dev < 0 || dev >= kMaxDevices) return GSPCA_ERR_NOT_SUPPORTED;
-    std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (g_scratch_addr[dev] == nullptr) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return GSPCA_ERR_CUDA;
-        int n = 0;
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
-            return GSPCA_ERR_CUDA;
-        g_num_sms[dev] = n;
-        g_scratch_addr[dev] = p;
-    }
-    *addr = g_scratch_addr[dev];
-    *sms = g_num_sms[dev];
+    void* p = nullptr;
+    if (!cuda_ok(cudaGetSymbolAddress(&p, g_noalloc_scratch))) return GSPCA_ERR_CUDA;
+    if (p == nullptr) return GSPCA_ERR_CUDA;
+    int n = 0;
+    if (!cuda_ok(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev))) return GSPCA_ERR_CUDA;
+    if (n < 1) return GSPCA_ERR_CUDA;
+    *addr = p;
+    *sms = n;
     return GSPCA_OK;
 }
 
@@ -55,19 +45,13 @@ extern "C" gspca_status gspca_fit_noalloc(void* stream, const float* X, gspca_la
     if ((layout == GSPCA_COL_MAJOR && ldx < M) || (layout == GSPCA_ROW_MAJOR && ldx < N) ||
         (layout != GSPCA_COL_MAJOR && layout != GSPCA_ROW_MAJOR))
         return GSPCA_ERR_INVALID_ARG;
-    if (opts) {
-        if (opts->warm) return GSPCA_ERR_NOT_SUPPORTED;  // its buffers are not part of the fixed scratch
-        if (opts->center < 0 || opts->center > 2 || opts->grid_ctas < 0 || opts->timeout_s < 0 ||
-            opts->test_stall < 0 || opts->test_stall > 1)
-            return GSPCA_ERR_INVALID_ARG;
-        if (opts->iters_lock)
-            for (int k = 0; k < K; ++k)
-                if (opts->iters_lock[k] < 1) return GSPCA_ERR_INVALID_ARG;
-    }
+    const gspca_status ost = check_opts(opts, K);
+    if (ost != GSPCA_OK) return ost;
+    if (opts && opts->warm) return GSPCA_ERR_NOT_SUPPORTED;  // its buffers are not part of the fixed scratch
     if (N > kMaxCols) return GSPCA_ERR_NOT_SUPPORTED;
 
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return GSPCA_ERR_CUDA;
+    if (!cuda_ok(cudaGetDevice(&dev))) return GSPCA_ERR_CUDA;
     void* scratch = nullptr;
     int sms = 0;
     gspca_status st = device_setup(dev, &scratch, &sms);
@@ -77,7 +61,8 @@ extern "C" gspca_status gspca_fit_noalloc(void* stream, const float* X, gspca_la
     // launch shape first (it fixes the grid, hence the partial buffers), then
     // the workspace for exactly this problem, checked against the array's size
     Plan plan{};
-    if (plan_fit(dev, sms, sms, M, N, K, cell_bytes(GSPCA_F32), algo == GSPCA_GS, ws_ld(K), opts, &plan) != cudaSuccess) return GSPCA_ERR_CUDA;
+    if (!cuda_ok(plan_fit(dev, sms, sms, M, N, K, cell_bytes(GSPCA_F32), algo == GSPCA_GS, ws_ld(K), opts, &plan)))
+        return GSPCA_ERR_CUDA;
     const WsDims dims{(long)(M + 3) / 4 * 4, N, K, plan.G};
     if (carve(nullptr, dims).bytes > (size_t)GSPCA_NOALLOC_SCRATCH_BYTES) return GSPCA_ERR_NOT_SUPPORTED;
     const Workspace w = carve(scratch, dims);
@@ -86,23 +71,24 @@ extern "C" gspca_status gspca_fit_noalloc(void* stream, const float* X, gspca_la
 
     const int* lock_dev = nullptr;
     if (opts && opts->iters_lock) {
-        if (cudaMemcpyAsync(w.lock, opts->iters_lock, sizeof(int) * K, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        if (!cuda_ok(cudaMemcpyAsync(w.lock, opts->iters_lock, sizeof(int) * K, cudaMemcpyHostToDevice, s)))
             return GSPCA_ERR_CUDA;
         lock_dev = w.lock;
     }
     const double timeout = (opts && opts->timeout_s > 0) ? opts->timeout_s : 2.0;
     FitArgs a = make_args(w, plan, M, N, K, tol, max_iter, algo, lock_dev, timeout, nxpart);
-    if (opts && opts->test_stall) a.stall_word = w.abort + 2;  // a word nothing sets
+    // a word nothing sets: the pack kernel clears all four abort words
+    if (opts && opts->test_stall) a.stall_word = w.abort + 2;
     int launches = 0;
     // the pack kernel, first in the sequence, clears the barrier, abort and status words
-    if (enqueue_sequence(w, plan, a, s, X, layout, ldx, opts ? opts->center : 0, T, P, lambda, iters, R_out,
-                         nullptr, nullptr, &launches) != cudaSuccess)
+    if (!cuda_ok(enqueue_sequence(w, plan, a, s, X, layout, ldx, opts ? opts->center : 0, T, P, lambda, iters, R_out,
+                                  nullptr, nullptr, &launches)))
         return GSPCA_ERR_CUDA;
 
     int words[kInfoWords + 1] = {0};
-    if (cudaMemcpyAsync(words, w.info, sizeof(int) * kInfoWords, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(words + kInfoWords, w.abort, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
+    if (!cuda_ok(cudaMemcpyAsync(words, w.info, sizeof(int) * kInfoWords, cudaMemcpyDeviceToHost, s)) ||
+        !cuda_ok(cudaMemcpyAsync(words + kInfoWords, w.abort, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+        !cuda_ok(cudaStreamSynchronize(s)))
         return GSPCA_ERR_CUDA;
     if (words[kInfoWords] != 0) return GSPCA_ERR_TIMEOUT;
     if (words[kInfoStatus] == kStDegenerate) return GSPCA_ERR_DEGENERATE;

@@ -39,8 +39,9 @@ static __global__ void rowmean_kernel(const float* X, int layout, long ldx, int 
 // zero, Cell<E> storage), with optional subtraction of column means (center 1)
 // or row means (center 2).  Each block writes the FP64 sum of squares of its
 // tile (of the stored values) to xpart.  Block
-// (0,0) also clears the fit kernel's barrier words (one every 32), abort flag
-// and info words: everything the fit needs to start at zero.
+// (0,0) also clears the fit kernel's barrier words (one every 32), the four
+// abort words (the flag and the testing hook's stall word) and the info words:
+// everything the fit needs to start at zero.
 // Tile: 32 columns x 32 panels (128 rows); 256 threads.
 template <class E>
 __global__ void __launch_bounds__(kPackThreads) pack_kernel(const float* __restrict__ X, int layout, long ldx,
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const float* __restr
     const int c0 = blockIdx.x * 32, p0 = blockIdx.y * 32, rbase = p0 * 4;
     if (blockIdx.x == 0 && blockIdx.y == 0) {
         for (int i = t; i < nflags; i += kPackThreads) flags[(size_t)i * 32] = 0u;
-        if (t == 0) *abort = 0;
+        if (t < 4) abort[t] = 0;  // the abort flag and the spare words after it
         if (t < ninfo) info[t] = 0;
     }
     float sq = 0.f;

@@ -235,28 +235,6 @@ def test_wait_limit_returns_timeout_status(gp):
         assert r2.status in (0, 4)
 
 
-def test_full_size_10000x2000(gp):
-    """The benchmark workload in the benchmark's launch configuration: every component
-    checked by invariants, the first three against the oracle replaying the GPU's counts."""
-    w = synth.WORKLOADS["planted_10000x2000"]
-    X32 = w.make().astype(np.float32)
-    g = run_gpu(gp, X32, w.K, "gs", w.tol, w.max_iter, want_R=True)
-    assert g["status"] in (0, 4)
-    assert g["info"]["found"] == w.K
-    K = w.K
-    P, T, lam = g["P"], g["T"], g["lam"]
-    assert np.abs(P.T @ P - np.eye(K)).max() <= ORTHO
-    G = T.T @ T
-    assert np.abs(G - np.diag(lam ** 2)).max() <= 1e-4 * lam[0] ** 2
-    xn = np.linalg.norm(X32)
-    assert np.linalg.norm(X32 - T @ P.T - g["R"]) <= 1e-5 * xn
-    ref = oracle.fit(X32.astype(np.float64), 3, tol=w.tol, max_iter=w.max_iter, algo="gs",
-                     iters_lock=g["iters"][:3])
-    for k in range(3):
-        assert abs(lam[k] - ref.lam[k]) <= SIG_REL * ref.lam[k]
-        assert angle(P[:, k], ref.P[:, k]) <= ANGLE
-
-
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 @pytest.mark.parametrize("shape", [(1003, 517, 6), (700, 2000, 4), (500, 3000, 3), (64, 4097, 3), (300, 7500, 3)])
 def test_load_path_gives_the_same_fit(gp, shape, storage):
