@@ -49,7 +49,9 @@ def _load():
             ip = ctypes.POINTER(ctypes.c_int)
             lib.oracle_fit.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int,
-                                       dp, dp, ip, dp, dp, dp, dp, ip, dp, ip]
+                                       ctypes.c_int, dp, dp, ip, dp, dp, dp, dp, ip, dp, ip]
+            lib.oracle_cgs.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int]
+            lib.oracle_cgs.restype = ctypes.c_int
             lib.oracle_ws_nparams.restype = ctypes.c_int
             lib.oracle_ws_features.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp]
             lib.oracle_ws_features.restype = ctypes.c_int
@@ -99,8 +101,12 @@ STORAGE = {"f64": 0, "bf16": 1}
 
 
 def fit(X: np.ndarray, K: int, tol: float = 1e-6, max_iter: int = 1000, algo: int | str = GS,
-        center: int = CENTER_NONE, iters_lock=None, storage: str = "f64", ws_net=None, ws_G=None) -> Fit:
+        center: int = CENTER_NONE, iters_lock=None, storage: str = "f64", ws_net=None, ws_G=None,
+        gs_passes: int = 1) -> Fit:
     """Run NIPALS-PCA (algo=0/'nipals') or GS-PCA (algo=1/'gs') on X (M×N) in FP64.
+
+    gs_passes (GS-PCA): classical Gram-Schmidt passes per half-iteration, 1 as in the
+    Sec. 2.3 pseudo-code, 2 for the iterated form (CGS2).
 
     storage="bf16": the residual R is rounded to bfloat16 after centring and after
     every deflation (Eq. 3); all arithmetic stays FP64.
@@ -131,7 +137,7 @@ def fit(X: np.ndarray, K: int, tol: float = 1e-6, max_iter: int = 1000, algo: in
         rho = np.zeros(2 * K, dtype=np.float64)
     nul = ctypes.POINTER(ctypes.c_double)()
     st = _load().oracle_fit(algo, _dptr(X), M, N, K, float(tol), int(max_iter), int(center),
-                            _iptr(lock), STORAGE[storage], _dptr(net) if net is not None else nul,
+                            _iptr(lock), STORAGE[storage], int(gs_passes), _dptr(net) if net is not None else nul,
                             _dptr(G) if G is not None else nul, _iptr(choice), _dptr(rho) if rho is not None else nul,
                             _dptr(T), _dptr(P), _dptr(lam), _iptr(iters), _dptr(R), _iptr(found))
     if st == 1:
@@ -182,6 +188,17 @@ def ws_adam(net, m, v, grad, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     """One Adam step in place on float64 arrays net, m, v."""
     _load().oracle_ws_adam(_dptr(net), _dptr(m), _dptr(v), _dptr(np.ascontiguousarray(grad, dtype=np.float64)),
                            int(t), float(lr), float(b1), float(b2), float(eps), len(net))
+
+
+def cgs(Q: np.ndarray, x: np.ndarray, passes: int = 1):
+    """`passes` classical Gram-Schmidt passes of x against the columns of Q: (x', last coefficients)."""
+    Q = np.asfortranarray(np.asarray(Q, dtype=np.float64))
+    rows, k = Q.shape
+    xx = np.array(x, dtype=np.float64, copy=True)
+    coef = np.zeros(k)
+    if _load().oracle_cgs(_dptr(Q), rows, k, _dptr(xx), _dptr(coef), int(passes)) != 0:
+        raise ValueError("oracle_cgs: invalid argument")
+    return xx, coef
 
 
 def round_bf16(x) -> np.ndarray:

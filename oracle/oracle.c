@@ -20,7 +20,10 @@
  *         lambda starting at 0, at most max_iter iterations (the test used in
  *         all four appendix programs; Sec. 2.2/2.3 print it as absolute);
  *       * Gram-Schmidt: one classical pass per half-iteration (Sec. 2.3
- *         pseudo-code, as in the appendix programs);
+ *         pseudo-code, as in the appendix programs); gs_passes = 2 applies
+ *         the classical pass twice ("applied iteratively", the remark of
+ *         Sec. 2.3 before the GS-PCA pseudo-code), every pass taking its
+ *         coefficients from the vector the previous pass left;
  *       * zero start column: when column k of the residual is exactly zero,
  *         start from the residual column of largest norm (lowest index on
  *         ties); when every column is zero the fit stops as degenerate;
@@ -149,6 +152,18 @@ static void cgs_pass(const double *Q, int rows, int k, double *x, double *coef)
         for (int r = 0; r < rows; r++)
             x[r] -= q[r] * coef[j];
     }
+}
+
+/* Exported for the pins: `passes` classical Gram-Schmidt passes of x against
+ * the first k columns of Q (rows x k, column-major).  coef receives the
+ * coefficients of the last pass.  Returns 0, or 1 on bad arguments. */
+int oracle_cgs(const double *Q, int rows, int k, double *x, double *coef, int passes)
+{
+    if (!Q || !x || !coef || rows < 1 || k < 1 || passes < 1)
+        return 1;
+    for (int p = 0; p < passes; p++)
+        cgs_pass(Q, rows, k, x, coef);
+    return 0;
 }
 
 static double frob(const double *A, int rows, int cols)
@@ -306,10 +321,10 @@ static int nipals(double *R, int M, int N, int K, double tol, int max_iter,
  *   R <- X
  *   for k: mu = 0; V(k) <- R(k)
  *     repeat: U(k) <- R^T V(k)
- *             if k>0: A <- U_(k)^T U(k); U(k) <- U(k) - U_(k) A
+ *             if k>0: A <- U_(k)^T U(k); U(k) <- U(k) - U_(k) A   (gs_passes times)
  *             U(k) <- U(k)/||U(k)||
  *             V(k) <- R U(k)
- *             if k>0: B <- V_(k)^T V(k); V(k) <- V(k) - V_(k) B
+ *             if k>0: B <- V_(k)^T V(k); V(k) <- V(k) - V_(k) B   (gs_passes times)
  *             lambda_k <- ||V(k)||; V(k) <- V(k)/lambda_k
  *             stop when converged; mu <- lambda_k
  *     R <- R - lambda_k V(k) U(k)^T
@@ -317,7 +332,7 @@ static int nipals(double *R, int M, int N, int K, double tol, int max_iter,
  * While a component is being extracted, column j < k of T holds V(j) (unit
  * norm); the scaling T = V Lambda happens once at the end. */
 static int gspca(double *R, int M, int N, int K, double tol, int max_iter,
-                 const int *iters_lock, double thresh, int storage,
+                 const int *iters_lock, double thresh, int storage, int gs_passes,
                  const double *ws_net, const double *ws_G, int *ws_choice, double *ws_rho,
                  double *T, double *P, double *lambda, int *iters, int *found)
 {
@@ -347,7 +362,7 @@ static int gspca(double *R, int M, int N, int K, double tol, int max_iter,
         int j = 0, degenerate = 0;
         for (;;) {
             gemv_t(R, M, N, v, u);
-            if (k > 0)
+            for (int pass = 0; k > 0 && pass < gs_passes; pass++)
                 cgs_pass(P, N, k, u, coef);
             double nu = nrm2(u, N);
             if (nu == 0.0) {
@@ -356,7 +371,7 @@ static int gspca(double *R, int M, int N, int K, double tol, int max_iter,
             }
             scal(u, N, 1.0 / nu);
             gemv_n(R, M, N, u, v);
-            if (k > 0)
+            for (int pass = 0; k > 0 && pass < gs_passes; pass++)
                 cgs_pass(T, M, k, v, coef);
             lam = nrm2(v, M);
             if (lam <= thresh) {
@@ -397,14 +412,16 @@ static int gspca(double *R, int M, int N, int K, double tol, int max_iter,
  * iters_lock (nullable): run exactly iters_lock[k] iterations for component k
  * and ignore the convergence test (used to replay another implementation's
  * iteration counts).  storage: 0 = R kept in FP64; 1 = R rounded to bfloat16
- * after centring and after every deflation.  ws_net / ws_G (nullable, GS-PCA
+ * after centring and after every deflation.  gs_passes (GS-PCA): classical
+ * Gram-Schmidt passes per half-iteration, 1 (the pseudo-code) or 2 (CGS2).
+ * ws_net / ws_G (nullable, GS-PCA
  * only): parameters and sketch of the learned warm start (warmstart.c);
  * ws_choice (K ints) and ws_rho (2K doubles) receive, per component, whether
  * the learned start was used and the two Rayleigh quotients compared.
  * Outputs: T (M x K), P (N x K), lambda (K), iters (K), found (number of
  * components extracted). */
 int oracle_fit(int algo, const double *X, int M, int N, int K, double tol, int max_iter,
-               int center, const int *iters_lock, int storage,
+               int center, const int *iters_lock, int storage, int gs_passes,
                const double *ws_net, const double *ws_G, int *ws_choice, double *ws_rho,
                double *T, double *P, double *lambda, int *iters, double *R, int *found)
 {
@@ -415,6 +432,8 @@ int oracle_fit(int algo, const double *X, int M, int N, int K, double tol, int m
     if (algo != 0 && algo != 1)
         return OR_INVALID;
     if (storage != 0 && storage != 1)
+        return OR_INVALID;
+    if (gs_passes != 1 && gs_passes != 2)
         return OR_INVALID;
     if (ws_net && (algo != 1 || !ws_G))
         return OR_INVALID;
@@ -433,8 +452,8 @@ int oracle_fit(int algo, const double *X, int M, int N, int K, double tol, int m
     double thresh = 64.0 * DBL_EPSILON * frob(R, M, N);
     if (algo == 0)
         return nipals(R, M, N, K, tol, max_iter, iters_lock, thresh, storage, T, P, lambda, iters, found);
-    return gspca(R, M, N, K, tol, max_iter, iters_lock, thresh, storage, ws_net, ws_G, ws_choice, ws_rho, T, P,
-                 lambda, iters, found);
+    return gspca(R, M, N, K, tol, max_iter, iters_lock, thresh, storage, gs_passes, ws_net, ws_G, ws_choice, ws_rho,
+                 T, P, lambda, iters, found);
 }
 
 /* ------------------------------------------------------- Jacobi eigensolver */
