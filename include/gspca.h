@@ -135,6 +135,13 @@ typedef struct {
                                where that is numerically safe, by keeping Q = R U, Z = U^T W and
                                V^T V up to date per component; otherwise three), 1 = always the
                                three-reduction step of Sec. 2.3.  The two agree to FP32 rounding. */
+    int gs_passes;          /* GS-PCA, single-problem entry points: classical Gram-Schmidt passes per
+                               half-iteration.  0 or 1 = one pass (the Sec. 2.3 pseudo-code and the
+                               appendix programs); 2 = the iterated form Sec. 2.3 mentions (CGS2):
+                               the second pass takes its coefficients from the vector the first
+                               pass left, at the cost of one more grid-wide reduction per
+                               half-iteration (it implies the three-reduction step).  The batched
+                               entry points accept 0 or 1 only (GSPCA_ERR_NOT_SUPPORTED). */
 } gspca_opts;
 
 /* Per-call record of the last fit on a handle (host memory). */

@@ -59,7 +59,7 @@ class Opts(ctypes.Structure):
                 ("grid_ctas", ctypes.c_int), ("timeout_s", ctypes.c_double),
                 ("cluster_ctas", ctypes.c_int), ("batch_pass", ctypes.c_int), ("test_stall", ctypes.c_int),
                 ("warm", ctypes.POINTER(WarmStartC)), ("resident", ctypes.c_int), ("load_path", ctypes.c_int),
-                ("gs_step", ctypes.c_int)]
+                ("gs_step", ctypes.c_int), ("gs_passes", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -150,8 +150,9 @@ class WarmStart:
 
 
 def _opts(center=0, iters_lock=None, grid_ctas=0, timeout_s=0.0, cluster_ctas=0, test_stall=0, batch_pass=0,
-          warm=None, resident=0, load_path=0, gs_step=0):
+          warm=None, resident=0, load_path=0, gs_step=0, gs_passes=0):
     o = Opts()
+    o.gs_passes = int(gs_passes)
     o.resident = int(resident)
     o.load_path = int(load_path)
     o.gs_step = int(gs_step)
@@ -220,9 +221,10 @@ def gspca_fit(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="
               center: int = 0, iters_lock=None, want_R: bool = False, grid_ctas: int = 0,
               timeout_s: float = 0.0, stream=None, check: bool = True, test_stall: int = 0,
               warm: WarmStart | None = None, resident: int = 0, load_path: int = 0,
-              gs_step: int = 0) -> FitResult:
+              gs_step: int = 0, gs_passes: int = 0) -> FitResult:
     """Fit K components of X (a float32 CUDA tensor, any 2-D strided layout).  `warm`: the
-    learned warm start (GS-PCA); the result's ws_choice marks the components that used it."""
+    learned warm start (GS-PCA); the result's ws_choice marks the components that used it.
+    `gs_passes=2`: two classical Gram-Schmidt passes per half-iteration (CGS2)."""
     import torch
 
     if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
@@ -243,7 +245,7 @@ def gspca_fit(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="
     choice = torch.zeros(K, device=dev, dtype=torch.int32) if warm is not None else None
     o, keep = _opts(center, iters_lock, grid_ctas, timeout_s, 0, test_stall,
                     warm=warm.c_struct(choice) if warm is not None else None, resident=resident,
-                    load_path=load_path, gs_step=gs_step)
+                    load_path=load_path, gs_step=gs_step, gs_passes=gs_passes)
     st = load().gspca_fit(ctypes.c_void_p(h), ctypes.c_void_p(stream), ctypes.c_void_p(X.data_ptr()),
                           layout, int(ldx), M, N, int(K), float(tol), int(max_iter), _ALGOS[algo],
                           ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(P.data_ptr()),
@@ -257,7 +259,7 @@ def gspca_fit(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="
 
 def gspca_fit_host(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="gs",
                    center: int = 0, iters_lock=None, want_R: bool = False, stream=None,
-                   out=None, check: bool = True) -> FitResult:
+                   out=None, check: bool = True, gs_passes: int = 0) -> FitResult:
     """Same as gspca_fit with host memory: X a float32 numpy array or CPU tensor (pinned is
     fastest); outputs are host arrays (reused from `out` when given)."""
     import numpy as np
@@ -286,7 +288,7 @@ def gspca_fit_host(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, a
                "R": np.empty((N, M), np.float32) if want_R else None}
     if stream is None and torch is not None and torch.cuda.is_available():
         stream = torch.cuda.current_stream().cuda_stream
-    o, keep = _opts(center, iters_lock)
+    o, keep = _opts(center, iters_lock, gs_passes=gs_passes)
     st = load().gspca_fit_host(ctypes.c_void_p(h), ctypes.c_void_p(stream), ctypes.c_void_p(xp), layout,
                                int(ldx), M, N, int(K), float(tol), int(max_iter), _ALGOS[algo],
                                ctypes.c_void_p(out["T"].ctypes.data), ctypes.c_void_p(out["P"].ctypes.data),
@@ -425,7 +427,7 @@ NOALLOC_SCRATCH_BYTES = 64 << 20
 
 def gspca_fit_noalloc(X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="gs", center: int = 0,
                       iters_lock=None, want_R: bool = False, stream=None, check: bool = True,
-                      timeout_s: float = 0.0, test_stall: int = 0) -> FitResult:
+                      timeout_s: float = 0.0, test_stall: int = 0, gs_passes: int = 0) -> FitResult:
     """gspca_fit without a handle and without any device allocation inside the library: the
     workspace is the library's fixed scratch array (NOALLOC_SCRATCH_BYTES per device).  For
     callers that must not allocate device memory.  Output tensors are the caller's (allocated
@@ -447,7 +449,7 @@ def gspca_fit_noalloc(X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="
     R = torch.empty((N, M), device=dev, dtype=torch.float32).t() if want_R else None
     if stream is None:
         stream = torch.cuda.current_stream(dev).cuda_stream
-    o, keep = _opts(center, iters_lock, timeout_s=timeout_s, test_stall=test_stall)
+    o, keep = _opts(center, iters_lock, timeout_s=timeout_s, test_stall=test_stall, gs_passes=gs_passes)
     with torch.cuda.device(dev):
         st = load().gspca_fit_noalloc(ctypes.c_void_p(stream), ctypes.c_void_p(X.data_ptr()), layout, int(ldx),
                                       M, N, int(K), float(tol), int(max_iter), _ALGOS[algo],

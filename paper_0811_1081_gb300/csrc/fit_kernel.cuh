@@ -100,6 +100,10 @@ struct FitArgs {
                               // matrices Z = U^T W and V^T V (ldk x ldk), kept up to date per component, and an
                               // iteration may form a' and ||v' - V b'||^2 from them (two grid-wide
                               // reductions per iteration instead of three)
+    int gs_passes;            // GS-PCA: classical Gram-Schmidt passes per half-iteration; 2 (CGS2, the
+                              // iterated form Sec. 2.3 mentions) takes the second pass's coefficients
+                              // from the vector the first pass left, one more grid-wide reduction per
+                              // half-iteration (three-reduction step only); 0 or 1: one pass
     // learned warm start (GS-PCA; all null when off)
     const float* ws_net;      // kWsParams network parameters
     const float* ws_G;        // sketch, M x 16 row-major
@@ -1775,6 +1779,41 @@ __device__ __forceinline__ void ring_setup(Ring& rg, SmemFit& sm, unsigned char*
     rg.issued = rg.used = 0;
 }
 
+// Second classical Gram-Schmidt pass (CGS2, FitArgs::gs_passes = 2) of the
+// vector x (global memory, entries a0 .. a1-1 owned by this CTA) against the
+// k factor columns A (this CTA's rows a0 .. a1-1, leading dimension lda):
+// partials A^T x -> partB[g][off, off + k), a team barrier, the reduced
+// coefficients -> kx (shared memory), then x <- x - A kx.  Returns in *sq the
+// CTA's sum of the new x^2 (every thread), false if a barrier failed.  Kept out
+// of line so that the one-pass kernels keep their register allocation.
+template <class Team>
+__device__ __noinline__ bool cgs_second_pass(const FitArgs& f, const Team& tm, SmemFit& sm, unsigned& epoch,
+                                             const float* A, int lda, int a0, int a1, int k, float* x, int off,
+                                             bool small_k, float* kx, ff* sq) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    __syncthreads();
+    rows_times_matrix(A, lda, a0, a1, k, [&](int r) { return ldcg(x + r); }, f.partB + (size_t)tm.g * f.LB + off, sm);
+    if (!tm.sync(epoch, &sm.flag)) return false;
+    if (small_k) {
+        gather_reduce(f, sm, tm.G, 0, 0, 0, f.partB + off, f.LB, k, [](int v) { return v; }, kx);
+    } else {
+        reduce_cols_distributed(f.partB, tm.G, tm.g, f.LB, off, k, f.red);
+        if (!tm.sync(epoch, &sm.flag)) return false;
+        for (int j = tid; j < k; j += T) kx[j] = (float)ldcg(f.red + j);
+        __syncthreads();
+    }
+    ff q = ff_zero();
+    matrix_times_vector(
+        A, lda, a0, a1, k, kx, [&](int r) { return ldcg(x + r); },
+        [&](int r, float s, float p) {
+            const float v = p - s;
+            x[r] = v;
+            q = ff_add(q, ff_sqr(v));
+        });
+    *sq = block_sum_ff(q, sm);
+    return true;
+}
+
 // Which first pass a team uses: the barrier-free one (pass_start_col) in the
 // single-problem kernel; the batched kernel keeps row_pass<kPassCol>, whose
 // register needs fit its larger state without spills.
@@ -1811,6 +1850,9 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
     float* rb = reinterpret_cast<float*>(dyn_smem + f.ring_bytes);
     // with the two-reduction step rb also holds c' after b', and 3 ldk floats follow ka
     const bool gs2 = kGs2Step<CPT, E, WARM, Team> && f.gs2 != 0;
+    // CGS2: a second classical pass on each half-iteration (never with the two-reduction step);
+    // compiled into the single-problem kernel only
+    const bool cgs2 = kStartColPass<Team> && f.algo == 1 && f.gs_passes == 2 && !gs2;
     float* ka = rb + f.max_slice + (gs2 ? 2 : 1) * f.ldk;
     float* kx3 = ka + f.ldk;
     const int nc1 = n1 - n0;
@@ -2086,6 +2128,15 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                     f.ut[(size_t)nb * N + n] = un;
                     nq = ff_add(nq, ff_sqr(un));
                 });
+            if (cgs2) {  // second pass on the first loading: a2 = U_(k)^T ut -> pB[ldk, 2 ldk)
+                ff q;
+                if (!cgs_second_pass(f, tm, sm, epoch, Ul, f.ldu, n0, n1, k, f.ut + (size_t)nb * N, f.ldk, small_k,
+                                     ka, &q)) {
+                    alive = false;
+                    goto leave;
+                }
+                nq = tid == 0 ? q : ff_zero();
+            }
         } else {
             for (int n = n0 + tid; n < n1; n += T) {
                 const float un = sv[n - n0] * xx_inv;
@@ -2247,13 +2298,30 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                     lam2p = sm.lam2s;  // s' - W b' is formed with the next loading below
                 } else {
                     ff l2 = ff_zero();
-                    matrix_times_vector(
-                        Vl, f.ldv, r0, r1, k, kb, [&](int r) { return ldcg(f.vraw + r); },
-                        [&](int r, float s, float p) {
-                            const float vc = p - s;
-                            f.vcorr[r] = vc;
-                            l2 = ff_add(l2, ff_sqr(vc));
-                        });
+                    if (!cgs2) {
+                        matrix_times_vector(
+                            Vl, f.ldv, r0, r1, k, kb, [&](int r) { return ldcg(f.vraw + r); },
+                            [&](int r, float s, float p) {
+                                const float vc = p - s;
+                                f.vcorr[r] = vc;
+                                l2 = ff_add(l2, ff_sqr(vc));
+                            });
+                    } else {
+                        // first pass v' - V b', then b2 = V^T (v' - V b') reduced across the grid and
+                        // the second pass (pB[2 ldk, 3 ldk)); the loading side then uses b' + b2
+                        matrix_times_vector(
+                            Vl, f.ldv, r0, r1, k, kb, [&](int r) { return ldcg(f.vraw + r); },
+                            [&](int r, float s, float p) { f.vcorr[r] = p - s; });
+                        ff q;
+                        if (!cgs_second_pass(f, tm, sm, epoch, Vl, f.ldv, r0, r1, k, f.vcorr, 2 * f.ldk, small_k,
+                                             ka, &q)) {
+                            alive = false;
+                            goto leave;
+                        }
+                        l2 = tid == 0 ? q : ff_zero();
+                        for (int jj = tid; jj < k; jj += T) kb[jj] += ka[jj];
+                        __syncthreads();
+                    }
                     matrix_times_vector(
                         Wl, f.ldw, n0, n1, k, kb, [&](int n) { return sv[n - n0]; },
                         [&](int n, float s, float p) { f.upre[n] = p - s; });
@@ -2359,6 +2427,13 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                 }
                 vinv_prev = vinv;
                 break;
+            }
+            if (cgs2 && k > 0) {  // second pass on the next loading: a2 = U_(k)^T ut -> pB[ldk, 2 ldk)
+                if (!cgs_second_pass(f, tm, sm, epoch, Ul, f.ldu, n0, n1, k, f.ut + (size_t)nbuf * N, f.ldk, small_k,
+                                     ka, &nq2)) {
+                    alive = false;
+                    goto leave;
+                }
             }
             mu = lamff;
             write_scalar(f, g, 2 + nbuf, nq2);

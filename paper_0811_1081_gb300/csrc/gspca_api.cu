@@ -135,18 +135,21 @@ gspca_status enqueue_fit(gspca_t h, cudaStream_t s, const float* X, gspca_layout
 // read of R (M x N values of elem_bytes each); per component one extra write
 // of R (the fused deflation); GS-PCA reads the FP32 factors V_(k) twice (b',
 // v') and U_(k) twice, W_(k) once per iteration.
-double alg_bytes(int M, int N, int found, const int* iters, bool gs, double elem_bytes) {
+// With two Gram-Schmidt passes (CGS2) every iteration reads V_(k) and U_(k)
+// twice more (the second pass's coefficients and its subtraction).
+double alg_bytes(int M, int N, int found, const int* iters, bool gs, double elem_bytes, int gs_passes) {
     const double mn = (double)M * N * elem_bytes;
     double b = 0.0;
     for (int k = 0; k < found; ++k) {
         const double passes = (double)iters[k] + 1.0;
         b += passes * mn + (k > 0 ? mn : 0.0);
         if (gs && k > 0) b += (double)iters[k] * (2.0 * M * k + 3.0 * N * k) * 4.0;
+        if (gs && k > 0 && gs_passes == 2) b += (double)iters[k] * (2.0 * M * k + 2.0 * N * k) * 4.0;
     }
     return b;
 }
 
-gspca_status finish(gspca_t h, cudaStream_t s, int K, gspca_algo algo, int M, int N) {
+gspca_status finish(gspca_t h, cudaStream_t s, int K, gspca_algo algo, int M, int N, const gspca_opts* opts) {
     GS_CUDA(cudaMemcpyAsync(h->h_info, h->ws.info, sizeof(int) * kInfoWords, cudaMemcpyDeviceToHost, s));
     GS_CUDA(cudaMemcpyAsync(h->h_info + kInfoWords, h->ws.abort, sizeof(int), cudaMemcpyDeviceToHost, s));
     int* hiters = h->h_info + kInfoWords + 4;
@@ -168,7 +171,8 @@ gspca_status finish(gspca_t h, cudaStream_t s, int K, gspca_algo algo, int M, in
     const int st = h->h_info[kInfoStatus];
     h->last.found = h->h_info[kInfoFound];
     h->last.total_iters = (long long)h->h_info[kInfoItersLo] + ((long long)h->h_info[kInfoItersHi] << 31);
-    h->last.alg_bytes = alg_bytes(M, N, h->last.found, hiters, algo == GSPCA_GS, cell_bytes(h->dtype) / 4.0);
+    h->last.alg_bytes = alg_bytes(M, N, h->last.found, hiters, algo == GSPCA_GS, cell_bytes(h->dtype) / 4.0,
+                                  (opts && opts->gs_passes == 2) ? 2 : 1);
     if (st == kStDegenerate) return GSPCA_ERR_DEGENERATE;
     if (st == kStNotConverged) return GSPCA_WARN_NOT_CONVERGED;
     return GSPCA_OK;
@@ -227,7 +231,7 @@ gspca_status gspca_fit(gspca_t h, void* stream, const float* X, gspca_layout lay
     cudaStream_t s = (cudaStream_t)stream;
     st = enqueue_fit(h, s, X, layout, ldx, M, N, K, tol, max_iter, algo, T, P, lambda, iters, R_out, opts);
     if (st != GSPCA_OK) return st;
-    return finish(h, s, K, algo, M, N);
+    return finish(h, s, K, algo, M, N, opts);
 }
 
 gspca_status gspca_fit_host(gspca_t h, void* stream, const float* X, gspca_layout layout, long ldx, int M, int N,
@@ -281,7 +285,7 @@ gspca_status gspca_fit_host(gspca_t h, void* stream, const float* X, gspca_layou
     GS_CUDA(cudaMemcpyAsync(lambda, h->slam, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
     if (iters) GS_CUDA(cudaMemcpyAsync(iters, h->siters, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
     if (R_out) GS_CUDA(cudaMemcpyAsync(R_out, h->sR, sizeof(float) * (size_t)M * N, cudaMemcpyDeviceToHost, s));
-    return finish(h, s, K, algo, M, N);
+    return finish(h, s, K, algo, M, N, opts);
 }
 
 gspca_status gspca_get_info(gspca_t h, gspca_info* info) {

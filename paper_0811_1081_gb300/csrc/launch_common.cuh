@@ -25,6 +25,7 @@ struct Plan {
     int cb;     // bytes of one cell of R: 16 (FP32 storage) or 8 (bfloat16 storage)
     bool warm;  // the kernel with the learned warm start
     int gs2;    // GS-PCA iterations may take the two-reduction step (see FitArgs::gs2)
+    int gs_passes;  // classical Gram-Schmidt passes per half-iteration (FitArgs::gs_passes)
     size_t dyn;
 };
 
@@ -59,7 +60,8 @@ inline gspca_status check_opts(const gspca_opts* opts, int K) {
     if (!opts) return GSPCA_OK;
     if (opts->center < 0 || opts->center > 2 || opts->grid_ctas < 0 || !(opts->timeout_s >= 0) ||
         opts->test_stall < 0 || opts->test_stall > 1 || opts->resident < 0 || opts->resident > 2 ||
-        opts->load_path < 0 || opts->load_path > 2 || opts->gs_step < 0 || opts->gs_step > 1)
+        opts->load_path < 0 || opts->load_path > 2 || opts->gs_step < 0 || opts->gs_step > 1 ||
+        opts->gs_passes < 0 || opts->gs_passes > 2)
         return GSPCA_ERR_INVALID_ARG;
     if (opts->iters_lock)
         for (int k = 0; k < K; ++k)
@@ -118,6 +120,7 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
                             const gspca_opts* opts, Plan* p) {
     p->cb = cb;
     p->warm = opts && opts->warm;
+    p->gs_passes = (opts && opts->gs_passes == 2) ? 2 : 1;
     p->cpt = cpt_for(N);
     p->ppr = p->cpt >= 8 ? 1 : 8 / p->cpt;
     const int np = (M + 3) / 4;
@@ -146,7 +149,8 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
         // rounding, which bfloat16 storage makes far larger than the step's own), up to
         // 4096 columns (wider rows are dominated by the pass over R)
         const size_t extra = sizeof(float) * ((size_t)4 * np_cta * ldf + 2 * (size_t)p->ldk * p->ldk);
-        if (!p->warm && cb == 16 && p->cpt <= 8 && (!opts || opts->gs_step == 0) && K <= kGs2MaxK &&
+        if (!p->warm && cb == 16 && p->cpt <= 8 && (!opts || opts->gs_step == 0) && p->gs_passes == 1 &&
+            K <= kGs2MaxK &&
             K <= kRedundantMax &&
             res + extra <= kResGs2MaxBytes) {
             p->gs2 = 1;
@@ -258,6 +262,7 @@ inline FitArgs make_args(const Workspace& w, const Plan& p, int M, int N, int K,
     a.dot_groups = p.groups;
     a.ring_bytes = (int)(p.dyn - vec_bytes(p.ldk, p.max_slice, p.gs2) - p.res);
     a.gs2 = p.gs2;
+    a.gs_passes = p.gs_passes;
     a.res_rows = p.res_rows;
     a.res_off = (int)(p.dyn - p.res);  // after the ring and the vectors
     a.ldk = p.ldk;

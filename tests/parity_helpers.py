@@ -41,10 +41,13 @@ def subspace_angle(A: np.ndarray, B: np.ndarray) -> float:
     return math.acos(min(1.0, float(s.min())))
 
 
-def clusters(lam_ref: np.ndarray, gap_rel: float) -> list[list[int]]:
+def clusters(lam_ref: np.ndarray, gap_rel: float, floor: float = 0.0) -> list[list[int]]:
     """Components grouped by their reference singular values: sorted descending,
-    neighbours closer than gap_rel (relative to the larger) share a group."""
-    order = [int(i) for i in np.argsort(-lam_ref)]
+    neighbours closer than gap_rel (relative to the larger) share a group.  With
+    floor > 0 only components with sigma >= floor * sigma_1 are grouped (the rest
+    are left out)."""
+    s1 = float(np.max(lam_ref)) if len(lam_ref) else 0.0
+    order = [int(i) for i in np.argsort(-lam_ref) if lam_ref[i] >= floor * s1]
     groups: list[list[int]] = []
     for i in order:
         if groups and (lam_ref[groups[-1][-1]] - lam_ref[i]) < gap_rel * lam_ref[groups[-1][-1]]:
