@@ -142,6 +142,12 @@ typedef struct {
                                pass left, at the cost of one more grid-wide reduction per
                                half-iteration (it implies the three-reduction step).  The batched
                                entry points accept 0 or 1 only (GSPCA_ERR_NOT_SUPPORTED). */
+    int svd_form;           /* single-problem entry points: 0 (default) = T holds the scores, T = V
+                               Lambda for GS-PCA and t_k for NIPALS-PCA; 1 = T holds the unit score
+                               directions, the SVD form X = V Lambda P^T + R of Eq. 5 (Sec. 2.3):
+                               V(k) for GS-PCA, t_k / lambda_k for NIPALS-PCA.  With K = N and every
+                               component converged, R vanishes and (T, lambda, P) is the full SVD.
+                               The batched entry points accept 0 only (GSPCA_ERR_NOT_SUPPORTED). */
 } gspca_opts;
 
 /* Per-call record of the last fit on a handle (host memory). */

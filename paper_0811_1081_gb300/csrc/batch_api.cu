@@ -119,6 +119,8 @@ gspca_status check_batch(gspca_t h, const gspca_problem* p, int count, double to
         if (opts->center != GSPCA_CENTER_NONE || opts->iters_lock) return GSPCA_ERR_NOT_SUPPORTED;
         if (opts->gs_passes < 0 || opts->gs_passes > 2) return GSPCA_ERR_INVALID_ARG;
         if (opts->gs_passes == 2) return GSPCA_ERR_NOT_SUPPORTED;  // one Gram-Schmidt pass in the batched kernel
+        if (opts->svd_form < 0 || opts->svd_form > 1) return GSPCA_ERR_INVALID_ARG;
+        if (opts->svd_form == 1) return GSPCA_ERR_NOT_SUPPORTED;  // the batched epilogue writes scores
         if (opts->timeout_s < 0 || opts->test_stall < 0 || opts->test_stall > 1) return GSPCA_ERR_INVALID_ARG;
         const int c = opts->cluster_ctas;
         if (c != 0 && c != 1 && c != 2 && c != 4 && c != 8 && c != 16) return GSPCA_ERR_INVALID_ARG;

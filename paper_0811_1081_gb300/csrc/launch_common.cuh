@@ -26,6 +26,7 @@ struct Plan {
     bool warm;  // the kernel with the learned warm start
     int gs2;    // GS-PCA iterations may take the two-reduction step (see FitArgs::gs2)
     int gs_passes;  // classical Gram-Schmidt passes per half-iteration (FitArgs::gs_passes)
+    int svd_form;   // 1: the epilogue writes the unit score directions (gspca_opts::svd_form)
     size_t dyn;
 };
 
@@ -61,7 +62,7 @@ inline gspca_status check_opts(const gspca_opts* opts, int K) {
     if (opts->center < 0 || opts->center > 2 || opts->grid_ctas < 0 || !(opts->timeout_s >= 0) ||
         opts->test_stall < 0 || opts->test_stall > 1 || opts->resident < 0 || opts->resident > 2 ||
         opts->load_path < 0 || opts->load_path > 2 || opts->gs_step < 0 || opts->gs_step > 1 ||
-        opts->gs_passes < 0 || opts->gs_passes > 2)
+        opts->gs_passes < 0 || opts->gs_passes > 2 || opts->svd_form < 0 || opts->svd_form > 1)
         return GSPCA_ERR_INVALID_ARG;
     if (opts->iters_lock)
         for (int k = 0; k < K; ++k)
@@ -121,6 +122,7 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
     p->cb = cb;
     p->warm = opts && opts->warm;
     p->gs_passes = (opts && opts->gs_passes == 2) ? 2 : 1;
+    p->svd_form = (opts && opts->svd_form == 1) ? 1 : 0;
     p->cpt = cpt_for(N);
     p->ppr = p->cpt >= 8 ? 1 : 8 / p->cpt;
     const int np = (M + 3) / 4;
@@ -302,7 +304,7 @@ inline cudaError_t enqueue_sequence(const Workspace& w, const Plan& p, FitArgs a
     if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return e;
     const dim3 egrid((M + 31) / 32 + (N + 31) / 32, (K + 31) / 32);
     epilogue_kernel<<<egrid, 256, 0, s>>>(w.V, w.ld, w.U, w.ld, w.lam, w.iters, w.info, M, N, K,
-                                          a.algo == GSPCA_GS, T, P, lambda, iters);
+                                          a.algo == GSPCA_GS, p.svd_form, T, P, lambda, iters);
     ++n;
     if (R_out) {
         if (p.cb == 8)

@@ -113,12 +113,14 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const float* __restr
 }
 
 // T (M x K, ld M), P (N x K, ld N), lambda, iters from the row-major
-// workspace factors.  Components >= found are zero.  mult: T = V * lambda_k
-// (GS) or T = V (NIPALS, V holds the unnormalised scores).
+// workspace factors.  Components >= found are zero.  T = V lambda_k (GS) or the
+// unnormalised scores t_k that the NIPALS workspace V holds; with svd set, the
+// unit score directions instead (the SVD form of Eq. 5): V (GS), t_k / lambda_k
+// (NIPALS).
 static __global__ void epilogue_kernel(const float* __restrict__ V, int ldv, const float* __restrict__ U, int ldu,
                                 const double* __restrict__ lam_ws, const int* __restrict__ iters_ws,
-                                const int* __restrict__ info, int M, int N, int K, int gs, float* T, float* P,
-                                double* lambda, int* iters) {
+                                const int* __restrict__ info, int M, int N, int K, int gs, int svd, float* T,
+                                float* P, double* lambda, int* iters) {
     __shared__ float tile[32][33];
     const int found = info[1];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 256 threads: 32 x 8
@@ -136,7 +138,8 @@ static __global__ void epilogue_kernel(const float* __restrict__ V, int ldv, con
         float v = 0.f;
         if (r < R && k < K && k < found) {
             v = S[(size_t)r * ld + k];
-            if (doT && gs) v = (float)((double)v * lam_ws[k]);
+            if (doT && gs && !svd) v = (float)((double)v * lam_ws[k]);        // T = V Lambda
+            else if (doT && !gs && svd) v = (float)((double)v / lam_ws[k]);  // t_k / lambda_k
         }
         tile[i][tx] = v;
     }
