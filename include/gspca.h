@@ -141,7 +141,8 @@ typedef struct {
                                the second pass takes its coefficients from the vector the first
                                pass left, at the cost of one more grid-wide reduction per
                                half-iteration (it implies the three-reduction step).  The batched
-                               entry points accept 0 or 1 only (GSPCA_ERR_NOT_SUPPORTED). */
+                               entry points, and the learned warm start, accept 0 or 1 only
+                               (GSPCA_ERR_NOT_SUPPORTED). */
     int svd_form;           /* single-problem entry points: 0 (default) = T holds the scores, T = V
                                Lambda for GS-PCA and t_k for NIPALS-PCA; 1 = T holds the unit score
                                directions, the SVD form X = V Lambda P^T + R of Eq. 5 (Sec. 2.3):

@@ -29,49 +29,73 @@ CENTER_NONE, CENTER_COLUMNS, CENTER_ROWS = 0, 1, 2
 STATUS = {0: "ok", 1: "invalid argument", 4: "not converged", 5: "degenerate"}
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so (gcc, -O2 as in the paper's Sec. 3 build line)."""
-    if force or not os.path.exists(_SO) or any(os.path.getmtime(_SO) < os.path.getmtime(f) for f in _SRCS):
-        cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
-               *_SRCS, "-o", _SO + ".tmp", "-lm"]
+# Builds of the same sources.  "O2" (the paper's optimisation level, Sec. 3,
+# single-threaded) is the checker every test uses; the others exist only to time
+# the oracle on the host cores: "O3", and "O2-omp" / "O3-omp" with OpenMP, whose
+# loops split over independent outputs so the results are the same bits.
+FLAVORS = {"O2": ["-O2"], "O3": ["-O3"], "O2-omp": ["-O2", "-fopenmp"], "O3-omp": ["-O3", "-fopenmp"]}
+
+
+def _so_path(flavor: str) -> str:
+    return _SO if flavor == "O2" else os.path.join(_HERE, f"liboracle_{flavor.replace('-', '_')}.so")
+
+
+def build(force: bool = False, flavor: str = "O2") -> str:
+    """Compile oracle.c into liboracle.so (gcc, -O2 as in the paper's Sec. 3 build line), or
+    one of the timing builds of FLAVORS."""
+    so = _so_path(flavor)
+    if force or not os.path.exists(so) or any(os.path.getmtime(so) < os.path.getmtime(f) for f in _SRCS):
+        cmd = ["gcc", *FLAVORS[flavor], "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
+               *_SRCS, "-o", so + ".tmp", "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(_SO + ".tmp", _SO)
-    return _SO
+        os.replace(so + ".tmp", so)
+    return so
 
 
-def _load():
+_flavors: dict = {}
+
+
+def _load(flavor: str = "O2"):
     global _lib
     with _lock:
+        if flavor != "O2":
+            if flavor not in _flavors:
+                _flavors[flavor] = _bind(ctypes.CDLL(build(flavor=flavor)))
+            return _flavors[flavor]
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_SO)
-            dp = ctypes.POINTER(ctypes.c_double)
-            ip = ctypes.POINTER(ctypes.c_int)
-            lib.oracle_fit.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int,
-                                       ctypes.c_int, dp, dp, ip, dp, dp, dp, dp, ip, dp, ip]
-            lib.oracle_cgs.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int]
-            lib.oracle_cgs.restype = ctypes.c_int
-            lib.oracle_ws_nparams.restype = ctypes.c_int
-            lib.oracle_ws_features.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp]
-            lib.oracle_ws_features.restype = ctypes.c_int
-            lib.oracle_ws_forward.argtypes = [dp, dp, ctypes.c_int, dp]
-            lib.oracle_ws_forward.restype = None
-            lib.oracle_ws_loss_grad.argtypes = [dp, dp, dp, ip, ctypes.c_int, dp]
-            lib.oracle_ws_loss_grad.restype = ctypes.c_double
-            lib.oracle_ws_adam.argtypes = [dp, dp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                           ctypes.c_double, ctypes.c_double, ctypes.c_int]
-            lib.oracle_ws_adam.restype = None
-            lib.oracle_round_bf16.argtypes = [ctypes.c_double]
-            lib.oracle_round_bf16.restype = ctypes.c_double
-            lib.oracle_fit.restype = ctypes.c_int
-            lib.oracle_center.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
-            lib.oracle_center.restype = ctypes.c_int
-            lib.oracle_jacobi_eigh.argtypes = [dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                                               dp, dp]
-            lib.oracle_jacobi_eigh.restype = ctypes.c_int
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(_SO))
     return _lib
+
+
+def _bind(lib):
+    """Declare the argument and result types of the exported functions."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.oracle_fit.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_double, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int,
+                               ctypes.c_int, dp, dp, ip, dp, dp, dp, dp, ip, dp, ip]
+    lib.oracle_cgs.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int]
+    lib.oracle_cgs.restype = ctypes.c_int
+    lib.oracle_ws_nparams.restype = ctypes.c_int
+    lib.oracle_ws_features.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp]
+    lib.oracle_ws_features.restype = ctypes.c_int
+    lib.oracle_ws_forward.argtypes = [dp, dp, ctypes.c_int, dp]
+    lib.oracle_ws_forward.restype = None
+    lib.oracle_ws_loss_grad.argtypes = [dp, dp, dp, ip, ctypes.c_int, dp]
+    lib.oracle_ws_loss_grad.restype = ctypes.c_double
+    lib.oracle_ws_adam.argtypes = [dp, dp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    lib.oracle_ws_adam.restype = None
+    lib.oracle_round_bf16.argtypes = [ctypes.c_double]
+    lib.oracle_round_bf16.restype = ctypes.c_double
+    lib.oracle_fit.restype = ctypes.c_int
+    lib.oracle_center.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.oracle_center.restype = ctypes.c_int
+    lib.oracle_jacobi_eigh.argtypes = [dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                       dp, dp]
+    lib.oracle_jacobi_eigh.restype = ctypes.c_int
+    return lib
 
 
 def _dptr(a: np.ndarray):
@@ -102,7 +126,7 @@ STORAGE = {"f64": 0, "bf16": 1}
 
 def fit(X: np.ndarray, K: int, tol: float = 1e-6, max_iter: int = 1000, algo: int | str = GS,
         center: int = CENTER_NONE, iters_lock=None, storage: str = "f64", ws_net=None, ws_G=None,
-        gs_passes: int = 1) -> Fit:
+        gs_passes: int = 1, flavor: str = "O2") -> Fit:
     """Run NIPALS-PCA (algo=0/'nipals') or GS-PCA (algo=1/'gs') on X (M×N) in FP64.
 
     gs_passes (GS-PCA): classical Gram-Schmidt passes per half-iteration, 1 as in the
@@ -111,7 +135,8 @@ def fit(X: np.ndarray, K: int, tol: float = 1e-6, max_iter: int = 1000, algo: in
     storage="bf16": the residual R is rounded to bfloat16 after centring and after
     every deflation (Eq. 3); all arithmetic stays FP64.
     ws_net (5377 parameters) and ws_G (M×16 sketch): GS-PCA with the learned warm start
-    (warmstart.c)."""
+    (warmstart.c).
+    flavor: which build runs the fit (FLAVORS; the results do not depend on it)."""
     if isinstance(algo, str):
         algo = {"nipals": NIPALS, "gs": GS}[algo.lower()]
     X = np.asfortranarray(np.asarray(X, dtype=np.float64))
@@ -136,7 +161,7 @@ def fit(X: np.ndarray, K: int, tol: float = 1e-6, max_iter: int = 1000, algo: in
         choice = np.zeros(K, dtype=np.int32)
         rho = np.zeros(2 * K, dtype=np.float64)
     nul = ctypes.POINTER(ctypes.c_double)()
-    st = _load().oracle_fit(algo, _dptr(X), M, N, K, float(tol), int(max_iter), int(center),
+    st = _load(flavor).oracle_fit(algo, _dptr(X), M, N, K, float(tol), int(max_iter), int(center),
                             _iptr(lock), STORAGE[storage], int(gs_passes), _dptr(net) if net is not None else nul,
                             _dptr(G) if G is not None else nul, _iptr(choice), _dptr(rho) if rho is not None else nul,
                             _dptr(T), _dptr(P), _dptr(lam), _iptr(iters), _dptr(R), _iptr(found))

@@ -108,31 +108,46 @@ static void scal(double *x, int n, double alpha)
         x[i] *= alpha;
 }
 
+/* Multi-threaded builds (-fopenmp, used only to time the oracle on many host
+ * cores) split the loops below over independent output elements; every
+ * element still receives its terms in the same index order, so the results
+ * are the single-threaded ones bit for bit.  Without -fopenmp the pragmas are
+ * ignored.  Rows are split in blocks of ROW_BLOCK. */
+#define ROW_BLOCK 512
+
 /* y = A^T x for A (rows x cols), i.e. y[c] = sum_r A[r,c] x[r]  (gemv 't'). */
 static void gemv_t(const double *A, int rows, int cols, const double *x, double *y)
 {
+#pragma omp parallel for schedule(static) if (cols > 64)
     for (int c = 0; c < cols; c++)
         y[c] = dot(A + (size_t)c * rows, x, rows);
 }
 
 /* y = A x for A (rows x cols), i.e. y[r] = sum_c A[r,c] x[c]  (gemv 'n').
- * Every y[r] receives its terms in index order c = 0, 1, ...; the loop runs
- * over columns so that the column-major matrix is read contiguously. */
+ * Every y[r] receives its terms in index order c = 0, 1, ...; within a block
+ * of rows the loop runs over columns so that the column-major matrix is read
+ * contiguously. */
 static void gemv_n(const double *A, int rows, int cols, const double *x, double *y)
 {
-    for (int r = 0; r < rows; r++)
-        y[r] = 0.0;
-    for (int c = 0; c < cols; c++) {
-        const double *col = A + (size_t)c * rows;
-        const double xc = x[c];
-        for (int r = 0; r < rows; r++)
-            y[r] += col[r] * xc;
+    const int nb = (rows + ROW_BLOCK - 1) / ROW_BLOCK;
+#pragma omp parallel for schedule(static) if (nb > 1)
+    for (int b = 0; b < nb; b++) {
+        const int r0 = b * ROW_BLOCK, r1 = r0 + ROW_BLOCK < rows ? r0 + ROW_BLOCK : rows;
+        for (int r = r0; r < r1; r++)
+            y[r] = 0.0;
+        for (int c = 0; c < cols; c++) {
+            const double *col = A + (size_t)c * rows;
+            const double xc = x[c];
+            for (int r = r0; r < r1; r++)
+                y[r] += col[r] * xc;
+        }
     }
 }
 
 /* A <- A + alpha x y^T  (ger, Eq. 3 deflation). */
 static void ger(double *A, int rows, int cols, double alpha, const double *x, const double *y)
 {
+#pragma omp parallel for schedule(static) if (cols > 64)
     for (int c = 0; c < cols; c++) {
         double ay = alpha * y[c];
         double *col = A + (size_t)c * rows;
@@ -143,14 +158,20 @@ static void ger(double *A, int rows, int cols, double alpha, const double *x, co
 
 /* One classical Gram-Schmidt pass of x against the first k columns of Q
  * (Sec. 2.3): coef = Q_(k)^T x, then x <- x - Q_(k) coef.  All k coefficients
- * are taken from the unmodified x (classical, not modified, Gram-Schmidt). */
+ * are taken from the unmodified x (classical, not modified, Gram-Schmidt);
+ * every x[r] loses its k terms in order j = 0, 1, ... */
 static void cgs_pass(const double *Q, int rows, int k, double *x, double *coef)
 {
     gemv_t(Q, rows, k, x, coef);
-    for (int j = 0; j < k; j++) {
-        const double *q = Q + (size_t)j * rows;
-        for (int r = 0; r < rows; r++)
-            x[r] -= q[r] * coef[j];
+    const int nb = (rows + ROW_BLOCK - 1) / ROW_BLOCK;
+#pragma omp parallel for schedule(static) if (nb > 1)
+    for (int b = 0; b < nb; b++) {
+        const int r0 = b * ROW_BLOCK, r1 = r0 + ROW_BLOCK < rows ? r0 + ROW_BLOCK : rows;
+        for (int j = 0; j < k; j++) {
+            const double *q = Q + (size_t)j * rows;
+            for (int r = r0; r < r1; r++)
+                x[r] -= q[r] * coef[j];
+        }
     }
 }
 

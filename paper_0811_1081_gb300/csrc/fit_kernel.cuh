@@ -100,10 +100,6 @@ struct FitArgs {
                               // matrices Z = U^T W and V^T V (ldk x ldk), kept up to date per component, and an
                               // iteration may form a' and ||v' - V b'||^2 from them (two grid-wide
                               // reductions per iteration instead of three)
-    int gs_passes;            // GS-PCA: classical Gram-Schmidt passes per half-iteration; 2 (CGS2, the
-                              // iterated form Sec. 2.3 mentions) takes the second pass's coefficients
-                              // from the vector the first pass left, one more grid-wide reduction per
-                              // half-iteration (three-reduction step only); 0 or 1: one pass
     // learned warm start (GS-PCA; all null when off)
     const float* ws_net;      // kWsParams network parameters
     const float* ws_G;        // sketch, M x 16 row-major
@@ -1779,13 +1775,12 @@ __device__ __forceinline__ void ring_setup(Ring& rg, SmemFit& sm, unsigned char*
     rg.issued = rg.used = 0;
 }
 
-// Second classical Gram-Schmidt pass (CGS2, FitArgs::gs_passes = 2) of the
+// Second classical Gram-Schmidt pass (the CG2 kernel instantiations) of the
 // vector x (global memory, entries a0 .. a1-1 owned by this CTA) against the
 // k factor columns A (this CTA's rows a0 .. a1-1, leading dimension lda):
 // partials A^T x -> partB[g][off, off + k), a team barrier, the reduced
 // coefficients -> kx (shared memory), then x <- x - A kx.  Returns in *sq the
-// CTA's sum of the new x^2 (every thread), false if a barrier failed.  Kept out
-// of line so that the one-pass kernels keep their register allocation.
+// CTA's sum of the new x^2 (every thread), false if a barrier failed.
 template <class Team>
 __device__ __noinline__ bool cgs_second_pass(const FitArgs& f, const Team& tm, SmemFit& sm, unsigned& epoch,
                                              const float* A, int lda, int a0, int a1, int k, float* x, int off,
@@ -1831,7 +1826,12 @@ constexpr bool kGs2Step = kStartColPass<Team> && !WARM && CPT <= 8 && Cell<E>::k
 // degenerate threshold and this CTA's shared memory; the ring must be set up
 // for f.N.  Writes V, U, W and lambda/iters for k < found; returns the
 // outcome (identical in every CTA of the team).
-template <int CPT, class E, bool WARM, class Team>
+// CG2 (single-problem kernels only): GS-PCA takes two classical Gram-Schmidt
+// passes per half-iteration (CGS2, the iterated form Sec. 2.3 mentions), the
+// second pass's coefficients from the vector the first pass left, with one
+// more grid-wide reduction per half-iteration; the two-reduction step is off.
+// A compile-time variant, so the one-pass kernels carry none of its code.
+template <int CPT, class E, bool WARM, class Team, bool CG2 = false>
 __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, unsigned char* dyn_smem, Ring& rg,
                               float threshf, unsigned& epoch) {
     constexpr int PPR = PassShape<CPT>::PPR;
@@ -1849,10 +1849,8 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
     // reduced pass partials: this CTA's N-slice, then the k-vector (b' or the Gram row)
     float* rb = reinterpret_cast<float*>(dyn_smem + f.ring_bytes);
     // with the two-reduction step rb also holds c' after b', and 3 ldk floats follow ka
-    const bool gs2 = kGs2Step<CPT, E, WARM, Team> && f.gs2 != 0;
-    // CGS2: a second classical pass on each half-iteration (never with the two-reduction step);
-    // compiled into the single-problem kernel only
-    const bool cgs2 = kStartColPass<Team> && f.algo == 1 && f.gs_passes == 2 && !gs2;
+    const bool gs2 = kGs2Step<CPT, E, WARM, Team> && !CG2 && f.gs2 != 0;
+    const bool cgs2 = CG2 && f.algo == 1;  // a second classical pass on each half-iteration
     float* ka = rb + f.max_slice + (gs2 ? 2 : 1) * f.ldk;
     float* kx3 = ka + f.ldk;
     const int nc1 = n1 - n0;
@@ -2128,7 +2126,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                     f.ut[(size_t)nb * N + n] = un;
                     nq = ff_add(nq, ff_sqr(un));
                 });
-            if (cgs2) {  // second pass on the first loading: a2 = U_(k)^T ut -> pB[ldk, 2 ldk)
+            if constexpr (CG2) {  // second pass on the first loading: a2 = U_(k)^T ut -> pB[ldk, 2 ldk)
                 ff q;
                 if (!cgs_second_pass(f, tm, sm, epoch, Ul, f.ldu, n0, n1, k, f.ut + (size_t)nb * N, f.ldk, small_k,
                                      ka, &q)) {
@@ -2298,7 +2296,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                     lam2p = sm.lam2s;  // s' - W b' is formed with the next loading below
                 } else {
                     ff l2 = ff_zero();
-                    if (!cgs2) {
+                    if constexpr (!CG2) {
                         matrix_times_vector(
                             Vl, f.ldv, r0, r1, k, kb, [&](int r) { return ldcg(f.vraw + r); },
                             [&](int r, float s, float p) {
@@ -2428,11 +2426,13 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                 vinv_prev = vinv;
                 break;
             }
-            if (cgs2 && k > 0) {  // second pass on the next loading: a2 = U_(k)^T ut -> pB[ldk, 2 ldk)
-                if (!cgs_second_pass(f, tm, sm, epoch, Ul, f.ldu, n0, n1, k, f.ut + (size_t)nbuf * N, f.ldk, small_k,
-                                     ka, &nq2)) {
-                    alive = false;
-                    goto leave;
+            if constexpr (CG2) {
+                if (cgs2 && k > 0) {  // second pass on the next loading: a2 = U_(k)^T ut -> pB[ldk, 2 ldk)
+                    if (!cgs_second_pass(f, tm, sm, epoch, Ul, f.ldu, n0, n1, k, f.ut + (size_t)nbuf * N, f.ldk,
+                                         small_k, ka, &nq2)) {
+                        alive = false;
+                        goto leave;
+                    }
                 }
             }
             mu = lamff;
@@ -2451,8 +2451,9 @@ leave:
 
 // ------------------------------------------------------------------ kernels
 
-// Single problem, whole grid (cooperative launch).
-template <int CPT, class E, bool WARM>
+// Single problem, whole grid (cooperative launch).  CG2: two classical
+// Gram-Schmidt passes per half-iteration (see fit_one).
+template <int CPT, class E, bool WARM, bool CG2 = false>
 __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
     __shared__ SmemFit sm;
     extern __shared__ __align__(128) unsigned char dyn_smem[];
@@ -2480,7 +2481,7 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
     ring_setup(rg, sm, dyn_smem, f.tma_stages, f.dot_groups == 2 ? 1 : PassShape<CPT>::PPR,
                f.ldp * Cell<E>::kBytes);
     unsigned epoch = 0;
-    const FitOutcome r = fit_one<CPT, E, WARM>(f, tm, sm, dyn_smem, rg, threshf, epoch);
+    const FitOutcome r = fit_one<CPT, E, WARM, TeamGrid, CG2>(f, tm, sm, dyn_smem, rg, threshf, epoch);
 #ifdef GSPCA_PHASE_TIMING
     PHASE_MARK(15);
     if (blockIdx.x == 0 && tid == 0 && f.timing)

@@ -54,6 +54,7 @@ gspca_status check_fit_args(gspca_t h, const void* X, gspca_layout layout, long 
             const gspca_warm_start* w = opts->warm;
             if (!w->net || !w->G || w->G_rows < M) return GSPCA_ERR_INVALID_ARG;
             if (algo != GSPCA_GS || cpt_for(N) > kWarmMaxCpt) return GSPCA_ERR_NOT_SUPPORTED;
+            if (opts->gs_passes == 2) return GSPCA_ERR_NOT_SUPPORTED;  // no kernel has both
         }
     }
     return GSPCA_OK;

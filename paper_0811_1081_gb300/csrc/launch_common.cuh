@@ -25,7 +25,7 @@ struct Plan {
     int cb;     // bytes of one cell of R: 16 (FP32 storage) or 8 (bfloat16 storage)
     bool warm;  // the kernel with the learned warm start
     int gs2;    // GS-PCA iterations may take the two-reduction step (see FitArgs::gs2)
-    int gs_passes;  // classical Gram-Schmidt passes per half-iteration (FitArgs::gs_passes)
+    int gs_passes;  // classical Gram-Schmidt passes per half-iteration: 2 selects the CGS2 kernels
     int svd_form;   // 1: the epilogue writes the unit score directions (gspca_opts::svd_form)
     size_t dyn;
 };
@@ -73,9 +73,9 @@ inline gspca_status check_opts(const gspca_opts* opts, int K) {
 // Kernel attributes and launches per (columns per thread, storage type).  They
 // are defined beside the kernels (fit_inst.cuh) and instantiated once each in
 // the fit_*.cu translation units, so the host-side units compile no kernel.
-template <int CPT, class E, bool WARM>
+template <int CPT, class E, bool WARM, bool CG2>
 cudaError_t fit_attrs(size_t dyn, int* bps, int* static_smem);
-template <int CPT, class E, bool WARM>
+template <int CPT, class E, bool WARM, bool CG2>
 cudaError_t launch_fit_t(const FitArgs& a, int G, size_t dyn, cudaStream_t s);
 
 // The learned warm start is compiled into the fit kernels for up to this many
@@ -90,27 +90,37 @@ void launch_unpack(dim3 grid, cudaStream_t s, const void* R, int M, int N, int n
                    const float* U, int ldu, const double* lam, const int* info, int K, int gs, float* R_out);
 
 template <class E>
-inline cudaError_t fit_attrs_e(int cpt, bool warm, size_t dyn, int* bps, int* st) {
+inline cudaError_t fit_attrs_e(int cpt, bool warm, bool cg2, size_t dyn, int* bps, int* st) {
     if (warm) {
+        if (cg2) return cudaErrorInvalidValue;  // no kernel has both
         switch (cpt) {
-            case 1: return fit_attrs<1, E, true>(dyn, bps, st);
-            case 2: return fit_attrs<2, E, true>(dyn, bps, st);
-            case 4: return fit_attrs<4, E, true>(dyn, bps, st);
+            case 1: return fit_attrs<1, E, true, false>(dyn, bps, st);
+            case 2: return fit_attrs<2, E, true, false>(dyn, bps, st);
+            case 4: return fit_attrs<4, E, true, false>(dyn, bps, st);
             default: return cudaErrorInvalidValue;
         }
     }
+    if (cg2) {
+        switch (cpt) {
+            case 1: return fit_attrs<1, E, false, true>(dyn, bps, st);
+            case 2: return fit_attrs<2, E, false, true>(dyn, bps, st);
+            case 4: return fit_attrs<4, E, false, true>(dyn, bps, st);
+            case 8: return fit_attrs<8, E, false, true>(dyn, bps, st);
+            default: return fit_attrs<16, E, false, true>(dyn, bps, st);
+        }
+    }
     switch (cpt) {
-        case 1: return fit_attrs<1, E, false>(dyn, bps, st);
-        case 2: return fit_attrs<2, E, false>(dyn, bps, st);
-        case 4: return fit_attrs<4, E, false>(dyn, bps, st);
-        case 8: return fit_attrs<8, E, false>(dyn, bps, st);
-        default: return fit_attrs<16, E, false>(dyn, bps, st);
+        case 1: return fit_attrs<1, E, false, false>(dyn, bps, st);
+        case 2: return fit_attrs<2, E, false, false>(dyn, bps, st);
+        case 4: return fit_attrs<4, E, false, false>(dyn, bps, st);
+        case 8: return fit_attrs<8, E, false, false>(dyn, bps, st);
+        default: return fit_attrs<16, E, false, false>(dyn, bps, st);
     }
 }
 
-inline cudaError_t fit_attrs_any(int cpt, int cb, bool warm, size_t dyn, int* bps, int* st) {
-    return cb == 8 ? fit_attrs_e<__nv_bfloat16>(cpt, warm, dyn, bps, st)
-                   : fit_attrs_e<float>(cpt, warm, dyn, bps, st);
+inline cudaError_t fit_attrs_any(int cpt, int cb, bool warm, bool cg2, size_t dyn, int* bps, int* st) {
+    return cb == 8 ? fit_attrs_e<__nv_bfloat16>(cpt, warm, cg2, dyn, bps, st)
+                   : fit_attrs_e<float>(cpt, warm, cg2, dyn, bps, st);
 }
 
 // Grid size, ring depth and shared memory for one problem.  Gcap bounds the
@@ -164,7 +174,7 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
     cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (e != cudaSuccess) return e;
     int bps = 0, st = 0;
-    e = fit_attrs_any(p->cpt, cb, p->warm, vec, &bps, &st);
+    e = fit_attrs_any(p->cpt, cb, p->warm, p->gs_passes == 2, vec, &bps, &st);
     if (e != cudaSuccess) return e;
     const long avail = (long)optin - st - (long)vec - (long)p->res - 1024;
     // Preferred: the two-group loading pass with one panel per ring stage and an
@@ -191,7 +201,7 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
     }
     p->S = S;
     p->dyn = vec + p->res + (size_t)S * stage;
-    e = fit_attrs_any(p->cpt, cb, p->warm, p->dyn, &bps, &st);
+    e = fit_attrs_any(p->cpt, cb, p->warm, p->gs_passes == 2, p->dyn, &bps, &st);
     if (e != cudaSuccess) return e;
     if (bps < 1) return cudaErrorInvalidConfiguration;
     return cudaSuccess;
@@ -200,19 +210,29 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
 template <class E>
 inline cudaError_t launch_fit_e(const FitArgs& a, const Plan& p, cudaStream_t s) {
     if (p.warm) {
+        if (p.gs_passes == 2) return cudaErrorInvalidValue;  // no kernel has both
         switch (p.cpt) {
-            case 1: return launch_fit_t<1, E, true>(a, p.G, p.dyn, s);
-            case 2: return launch_fit_t<2, E, true>(a, p.G, p.dyn, s);
-            case 4: return launch_fit_t<4, E, true>(a, p.G, p.dyn, s);
+            case 1: return launch_fit_t<1, E, true, false>(a, p.G, p.dyn, s);
+            case 2: return launch_fit_t<2, E, true, false>(a, p.G, p.dyn, s);
+            case 4: return launch_fit_t<4, E, true, false>(a, p.G, p.dyn, s);
             default: return cudaErrorInvalidValue;
         }
     }
+    if (p.gs_passes == 2) {
+        switch (p.cpt) {
+            case 1: return launch_fit_t<1, E, false, true>(a, p.G, p.dyn, s);
+            case 2: return launch_fit_t<2, E, false, true>(a, p.G, p.dyn, s);
+            case 4: return launch_fit_t<4, E, false, true>(a, p.G, p.dyn, s);
+            case 8: return launch_fit_t<8, E, false, true>(a, p.G, p.dyn, s);
+            default: return launch_fit_t<16, E, false, true>(a, p.G, p.dyn, s);
+        }
+    }
     switch (p.cpt) {
-        case 1: return launch_fit_t<1, E, false>(a, p.G, p.dyn, s);
-        case 2: return launch_fit_t<2, E, false>(a, p.G, p.dyn, s);
-        case 4: return launch_fit_t<4, E, false>(a, p.G, p.dyn, s);
-        case 8: return launch_fit_t<8, E, false>(a, p.G, p.dyn, s);
-        default: return launch_fit_t<16, E, false>(a, p.G, p.dyn, s);
+        case 1: return launch_fit_t<1, E, false, false>(a, p.G, p.dyn, s);
+        case 2: return launch_fit_t<2, E, false, false>(a, p.G, p.dyn, s);
+        case 4: return launch_fit_t<4, E, false, false>(a, p.G, p.dyn, s);
+        case 8: return launch_fit_t<8, E, false, false>(a, p.G, p.dyn, s);
+        default: return launch_fit_t<16, E, false, false>(a, p.G, p.dyn, s);
     }
 }
 
@@ -264,7 +284,6 @@ inline FitArgs make_args(const Workspace& w, const Plan& p, int M, int N, int K,
     a.dot_groups = p.groups;
     a.ring_bytes = (int)(p.dyn - vec_bytes(p.ldk, p.max_slice, p.gs2) - p.res);
     a.gs2 = p.gs2;
-    a.gs_passes = p.gs_passes;
     a.res_rows = p.res_rows;
     a.res_off = (int)(p.dyn - p.res);  // after the ring and the vectors
     a.ldk = p.ldk;

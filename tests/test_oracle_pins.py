@@ -364,3 +364,17 @@ def test_bf16_storage_singular_values_within_weyl_bound(oracle_mod, algo):
         moved = max(moved, abs(fb.lam[k] - f64.lam[k]) / f64.lam[k])
     assert abs(fb.lam[0] - f64.lam[0]) <= 1e-10 * f64.lam[0]  # component 0 sees no deflation
     assert moved > 1e-9
+
+
+@pytest.mark.parametrize("flavor", ["O3", "O2-omp", "O3-omp"])
+@pytest.mark.parametrize("algo", ["gs", "nipals"])
+def test_timing_builds_give_the_checkers_bits(oracle_mod, flavor, algo):
+    """The builds that only time the oracle on the host (-O3, OpenMP) return the
+    single-threaded -O2 checker's results bit for bit: their parallel loops split over
+    independent outputs, every sum keeps its index order, and -ffp-contract=off keeps
+    one rounding per operation.  Shapes span several row blocks and parallel columns."""
+    X = synth.planted(1300, 150, 5.0, 0.85, 0.01, (7, 1300)).X
+    a = oracle_mod.fit(X, 6, algo=algo, gs_passes=1)
+    b = oracle_mod.fit(X, 6, algo=algo, gs_passes=1, flavor=flavor)
+    for key in ("T", "P", "lam", "iters", "R"):
+        assert np.array_equal(getattr(a, key), getattr(b, key)), key
