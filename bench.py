@@ -48,13 +48,17 @@ UNIT = "components/s"
 FALLBACK_HBM_GBS = 6800.0
 
 
-def kernel_name(N, storage="f32"):
+def kernel_name(N, storage="f32", K=1, gs_passes=1):
     """The instantiation of the persistent fit kernel for N columns (columns per thread),
-    the storage type of R, without the learned warm start."""
+    the storage type of R, without the learned warm start; CG2 for two Gram-Schmidt
+    passes, WIDE for more than 128 components."""
     cpt = 1
     while cpt * 512 < N:
         cpt *= 2
-    return f"fit_kernel<{cpt}, {'float' if storage == 'f32' else '__nv_bfloat16'}, false>"
+    cg2 = gs_passes == 2
+    wide = cg2 or K > 128
+    return (f"fit_kernel<{cpt}, {'float' if storage == 'f32' else '__nv_bfloat16'}, false, "
+            f"{'true' if cg2 else 'false'}, {'true' if wide else 'false'}>")
 
 
 def profile_stem(kernel):
@@ -598,7 +602,7 @@ def main():
 
     # roofline of the persistent kernel: algorithmic bytes / its event-timed duration
     peak, peak_src = measured_peaks()
-    kname = kernel_name(N, args.storage)
+    kname = kernel_name(N, args.storage, K)
     traffic, traffic_src = profiled_traffic(kname, w.name)
     if traffic_src:
         traffic_src = os.path.relpath(traffic_src, ROOT) + (" (sources changed since: null)" if traffic is None else "")

@@ -12,21 +12,21 @@
 
 namespace gspca {
 
-template <int CPT, class E, bool WARM, bool CG2>
+template <int CPT, class E, bool WARM, bool CG2, bool WIDE>
 cudaError_t fit_attrs(size_t dyn, int* bps, int* static_smem) {
     cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, fit_kernel<CPT, E, WARM, CG2>);
+    cudaError_t e = cudaFuncGetAttributes(&fa, fit_kernel<CPT, E, WARM, CG2, WIDE>);
     if (e != cudaSuccess) return e;
     *static_smem = (int)fa.sharedSizeBytes;
-    e = cudaFuncSetAttribute(fit_kernel<CPT, E, WARM, CG2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    e = cudaFuncSetAttribute(fit_kernel<CPT, E, WARM, CG2, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fit_kernel<CPT, E, WARM, CG2>, kBlock, dyn);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fit_kernel<CPT, E, WARM, CG2, WIDE>, kBlock, dyn);
 }
 
-template <int CPT, class E, bool WARM, bool CG2>
+template <int CPT, class E, bool WARM, bool CG2, bool WIDE>
 cudaError_t launch_fit_t(const FitArgs& a, int G, size_t dyn, cudaStream_t s) {
     void* args[] = {const_cast<FitArgs*>(&a)};
-    return cudaLaunchCooperativeKernel((const void*)fit_kernel<CPT, E, WARM, CG2>, dim3(G), dim3(kBlock), args, dyn,
+    return cudaLaunchCooperativeKernel((const void*)fit_kernel<CPT, E, WARM, CG2, WIDE>, dim3(G), dim3(kBlock), args, dyn,
                                        s);
 }
 
@@ -53,14 +53,23 @@ const void* batch_kernel_ptr() {
 
 // Explicit instantiation of the fit kernel of one column-block count / storage type
 // (WARM: with the learned warm start).
-#define GSPCA_INSTANTIATE_FIT(CPT, E, WARM)                                                                       \
-    template cudaError_t gspca::fit_attrs<CPT, E, WARM, false>(size_t, int*, int*);                               \
-    template cudaError_t gspca::launch_fit_t<CPT, E, WARM, false>(const gspca::FitArgs&, int, size_t, cudaStream_t);
+#define GSPCA_INSTANTIATE_FIT(CPT, E, WARM)                                                              \
+    template cudaError_t gspca::fit_attrs<CPT, E, WARM, false, false>(size_t, int*, int*);               \
+    template cudaError_t gspca::launch_fit_t<CPT, E, WARM, false, false>(const gspca::FitArgs&, int, size_t, \
+                                                                         cudaStream_t);
 
-// The fit kernel with two classical Gram-Schmidt passes per half-iteration (CGS2).
-#define GSPCA_INSTANTIATE_FIT_CGS2(CPT, E)                                                                        \
-    template cudaError_t gspca::fit_attrs<CPT, E, false, true>(size_t, int*, int*);                               \
-    template cudaError_t gspca::launch_fit_t<CPT, E, false, true>(const gspca::FitArgs&, int, size_t, cudaStream_t);
+// The fit kernel with two classical Gram-Schmidt passes per half-iteration (CGS2),
+// with the factor products for more than 128 components.
+#define GSPCA_INSTANTIATE_FIT_CGS2(CPT, E)                                                               \
+    template cudaError_t gspca::fit_attrs<CPT, E, false, true, true>(size_t, int*, int*);                \
+    template cudaError_t gspca::launch_fit_t<CPT, E, false, true, true>(const gspca::FitArgs&, int, size_t, \
+                                                                        cudaStream_t);
+
+// The fit kernel for more than 128 components (wide factor products).
+#define GSPCA_INSTANTIATE_FIT_WIDE(CPT, E)                                                                \
+    template cudaError_t gspca::fit_attrs<CPT, E, false, false, true>(size_t, int*, int*);               \
+    template cudaError_t gspca::launch_fit_t<CPT, E, false, false, true>(const gspca::FitArgs&, int, size_t, \
+                                                                         cudaStream_t);
 
 // Explicit instantiation of the pack/unpack kernels and the batched kernel of a storage type.
 #define GSPCA_INSTANTIATE_AUX(E)                                                                            \

@@ -994,9 +994,83 @@ __device__ __forceinline__ void rows_times_two(const float* A, const float* B, i
     __syncthreads();
 }
 
+// Past 128 columns (the leading dimension is then a multiple of 4, rows 16-byte
+// aligned) the products below take these forms: a thread owns columns and
+// sums its rows in index order (no cross-warp reduction), and a warp owns a
+// row and loads up to 1024 of its columns before using any, so a product
+// costs one or two L2 round trips instead of one per 64 or 128 columns.  They
+// are compiled into the WIDE kernel variants only (chosen for K > 128), so the
+// kernels for fewer components keep their code and register allocation.
 template <class Y>
+__device__ __forceinline__ void rows_times_matrix_wide(const float* A, int lda, int r0, int r1, int kk, Y y,
+                                                       float* dst) {
+    constexpr int RB = 16;
+    const int tid = threadIdx.x, T = blockDim.x;
+    for (int j0 = 0; j0 < kk; j0 += 2 * T) {
+        const int ja = j0 + tid, jb = ja + T;
+        float sa = 0.f, sb = 0.f;
+        for (int rb = r0; rb < r1; rb += RB) {
+            float a[RB], b[RB], yr[RB];
+#pragma unroll
+            for (int i = 0; i < RB; ++i) {
+                const int r = rb + i;
+                const bool ok = r < r1;
+                yr[i] = ok ? y(r) : 0.f;
+                a[i] = (ok && ja < kk) ? A[(size_t)r * lda + ja] : 0.f;
+                b[i] = (ok && jb < kk) ? A[(size_t)r * lda + jb] : 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < RB; ++i) {
+                sa = fmaf(a[i], yr[i], sa);
+                sb = fmaf(b[i], yr[i], sb);
+            }
+        }
+        if (ja < kk) dst[ja] = sa;
+        if (jb < kk) dst[jb] = sb;
+    }
+    __syncthreads();
+}
+
+template <class Pre, class Fn>
+__device__ __forceinline__ void matrix_times_vector_wide(const float* A, int lda, int r0, int r1, int kk,
+                                                         const float* x, Pre pre, Fn fn) {
+    constexpr int Q = 8;  // float4 per lane: 1024 columns per round trip
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = r0 + warp; r < r1; r += nw) {
+        const float pv = lane == 0 ? pre(r) : 0.f;
+        const float* ar = A + (size_t)r * lda;
+        float acc = 0.f;
+        for (int j0 = 0; j0 < kk; j0 += 128 * Q) {
+            float4 a[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int j = j0 + 4 * lane + 128 * q;
+                a[q] = j < kk ? *reinterpret_cast<const float4*>(ar + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int j = j0 + 4 * lane + 128 * q;
+                // columns at or past kk hold data of other components: not used
+                if (j < kk) acc = fmaf(a[q].x, x[j], acc);
+                if (j + 1 < kk) acc = fmaf(a[q].y, x[j + 1], acc);
+                if (j + 2 < kk) acc = fmaf(a[q].z, x[j + 2], acc);
+                if (j + 3 < kk) acc = fmaf(a[q].w, x[j + 3], acc);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (lane == 0) fn(r, acc, pv);
+    }
+}
+
+// WIDE: the wide forms are compiled in (the WIDE single-problem kernels).
+template <bool WIDE = false, class Y>
 __device__ __forceinline__ void rows_times_matrix(const float* A, int lda, int r0, int r1, int kk, Y y, float* dst,
                                                   SmemFit& sm) {
+    if (WIDE && kk > 128) {
+        rows_times_matrix_wide(A, lda, r0, r1, kk, y, dst);
+        return;
+    }
     if (vec_rows(lda, r1 - r0)) {
         rows_times_matrix_vec(A, lda, r0, r1, kk, y, dst, sm);
         return;
@@ -1040,9 +1114,13 @@ __device__ __forceinline__ void rows_times_matrix(const float* A, int lda, int r
 // r0 + warp + 16 i (i < 8 per block), issues all their loads (and pre(r))
 // first, and reduces the 8 row sums across lanes with one multi-value
 // butterfly.
-template <class Pre, class Fn>
+template <bool WIDE = false, class Pre, class Fn>
 __device__ __forceinline__ void matrix_times_vector(const float* A, int lda, int r0, int r1, int kk, const float* x,
                                                     Pre pre, Fn fn) {
+    if (WIDE && kk > 128) {
+        matrix_times_vector_wide(A, lda, r0, r1, kk, x, pre, fn);
+        return;
+    }
     if (vec_rows(lda, r1 - r0)) {
         matrix_times_vector_vec(A, lda, r0, r1, kk, x, pre, fn);
         return;
@@ -1787,7 +1865,7 @@ __device__ __noinline__ bool cgs_second_pass(const FitArgs& f, const Team& tm, S
                                              bool small_k, float* kx, ff* sq) {
     const int tid = threadIdx.x, T = blockDim.x;
     __syncthreads();
-    rows_times_matrix(A, lda, a0, a1, k, [&](int r) { return ldcg(x + r); }, f.partB + (size_t)tm.g * f.LB + off, sm);
+    rows_times_matrix<true>(A, lda, a0, a1, k, [&](int r) { return ldcg(x + r); }, f.partB + (size_t)tm.g * f.LB + off, sm);
     if (!tm.sync(epoch, &sm.flag)) return false;
     if (small_k) {
         gather_reduce(f, sm, tm.G, 0, 0, 0, f.partB + off, f.LB, k, [](int v) { return v; }, kx);
@@ -1798,7 +1876,7 @@ __device__ __noinline__ bool cgs_second_pass(const FitArgs& f, const Team& tm, S
         __syncthreads();
     }
     ff q = ff_zero();
-    matrix_times_vector(
+    matrix_times_vector<true>(
         A, lda, a0, a1, k, kx, [&](int r) { return ldcg(x + r); },
         [&](int r, float s, float p) {
             const float v = p - s;
@@ -1831,10 +1909,13 @@ constexpr bool kGs2Step = kStartColPass<Team> && !WARM && CPT <= 8 && Cell<E>::k
 // second pass's coefficients from the vector the first pass left, with one
 // more grid-wide reduction per half-iteration; the two-reduction step is off.
 // A compile-time variant, so the one-pass kernels carry none of its code.
-template <int CPT, class E, bool WARM, class Team, bool CG2 = false>
+// WIDE: the factor products take their wide forms past 128 components (the
+// kernel variant chosen for K > 128).
+template <int CPT, class E, bool WARM, class Team, bool CG2 = false, bool WIDE = false>
 __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, unsigned char* dyn_smem, Ring& rg,
                               float threshf, unsigned& epoch) {
     constexpr int PPR = PassShape<CPT>::PPR;
+    constexpr bool kWide = WIDE;
     const int G = tm.G, g = tm.g, tid = threadIdx.x, T = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int N = f.N, K = f.K;
@@ -1968,7 +2049,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
             write_scalar(f, g, 0, sc);
         }
         if (gs && k > 0)  // Gram row (V^T v_{k-1})_j over this CTA's rows
-            rows_times_matrix(Vl, f.ldv, r0, r1, k, [&](int r) { return Vl[(size_t)r * f.ldv + (k - 1)]; },
+            rows_times_matrix<kWide>(Vl, f.ldv, r0, r1, k, [&](int r) { return Vl[(size_t)r * f.ldv + (k - 1)]; },
                               pA + N, sm);
         if (defl) fence_proxy_async_global();
         GS_SYNC();
@@ -2079,7 +2160,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
             // u_pre = s0; a = U_(k)^T u_pre; ut = (u_pre - U a) / ||x||^2
             for (int n = n0 + tid; n < n1; n += T) f.upre[n] = sv[n - n0];
             __syncthreads();
-            rows_times_matrix(Ul, f.ldu, n0, n1, k, [&](int n) { return sv[n - n0]; }, pB, sm);
+            rows_times_matrix<kWide>(Ul, f.ldu, n0, n1, k, [&](int n) { return sv[n - n0]; }, pB, sm);
             GS_SYNC();
             if (small_k && gs2) {
                 gather_reduce<4>(f, sm, G, 0, 0, 0, f.partB, f.LB, 3 * k, ident, kx3);
@@ -2119,7 +2200,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                 for (int j = tid; j < k; j += T) ka[j] = (float)ldcg(f.red + j);
                 __syncthreads();
             }
-            matrix_times_vector(
+            matrix_times_vector<kWide>(
                 Ul, f.ldu, n0, n1, k, ka, [&](int n) { return sv[n - n0]; },
                 [&](int n, float s, float p) {
                     const float un = (p - s) * xx_inv;
@@ -2217,7 +2298,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
             if (try2)  // b' = V_(k)^T v' and c' = Q^T v' = U^T s' over this CTA's rows
                 rows_times_two(Vl, Ql, f.ldv, r0, r1, k, [&](int r) { return f.vraw[r]; }, pA + N, pA + N + k, sm);
             else if (gs && k > 0)  // b' = V_(k)^T v' over this CTA's rows
-                rows_times_matrix(Vl, f.ldv, r0, r1, k, [&](int r) { return f.vraw[r]; }, pA + N, sm);
+                rows_times_matrix<kWide>(Vl, f.ldv, r0, r1, k, [&](int r) { return f.vraw[r]; }, pA + N, sm);
             PHASE_MARK(3);
             GS_SYNC();
             PHASE_MARK(4);
@@ -2297,7 +2378,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                 } else {
                     ff l2 = ff_zero();
                     if constexpr (!CG2) {
-                        matrix_times_vector(
+                        matrix_times_vector<kWide>(
                             Vl, f.ldv, r0, r1, k, kb, [&](int r) { return ldcg(f.vraw + r); },
                             [&](int r, float s, float p) {
                                 const float vc = p - s;
@@ -2307,7 +2388,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                     } else {
                         // first pass v' - V b', then b2 = V^T (v' - V b') reduced across the grid and
                         // the second pass (pB[2 ldk, 3 ldk)); the loading side then uses b' + b2
-                        matrix_times_vector(
+                        matrix_times_vector<kWide>(
                             Vl, f.ldv, r0, r1, k, kb, [&](int r) { return ldcg(f.vraw + r); },
                             [&](int r, float s, float p) { f.vcorr[r] = p - s; });
                         ff q;
@@ -2320,11 +2401,11 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                         for (int jj = tid; jj < k; jj += T) kb[jj] += ka[jj];
                         __syncthreads();
                     }
-                    matrix_times_vector(
+                    matrix_times_vector<kWide>(
                         Wl, f.ldw, n0, n1, k, kb, [&](int n) { return sv[n - n0]; },
                         [&](int n, float s, float p) { f.upre[n] = p - s; });
                     __syncthreads();
-                    rows_times_matrix(Ul, f.ldu, n0, n1, k, [&](int n) { return f.upre[n]; }, pB, sm);
+                    rows_times_matrix<kWide>(Ul, f.ldu, n0, n1, k, [&](int n) { return f.upre[n]; }, pB, sm);
                     l2 = block_sum_ff(l2, sm);
                     write_scalar(f, g, 1, l2);
                     PHASE_MARK(7);
@@ -2380,7 +2461,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                         nq2 = ff_add(nq2, ff_sqr(un));
                     });
             } else {
-                matrix_times_vector(
+                matrix_times_vector<kWide>(
                     Ul, f.ldu, n0, n1, k, ka, [&](int n) { return ldcg(f.upre + n); },
                     [&](int n, float s, float p) {
                         const float un = (p - s) * nscale;
@@ -2400,7 +2481,7 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                 if (stop == 3 && status == kStOK) status = kStNotConverged;
                 // finalize component k: V(k), U(k), lambda_k, iters_k
                 if (step2) {  // v' - V b' for this CTA's rows (the two-reduction step skipped it)
-                    matrix_times_vector(
+                    matrix_times_vector<kWide>(
                         Vl, f.ldv, r0, r1, k, kb, [&](int r) { return ldcg(f.vraw + r); },
                         [&](int r, float s, float p) { f.vcorr[r] = p - s; });
                     __syncthreads();
@@ -2452,8 +2533,9 @@ leave:
 // ------------------------------------------------------------------ kernels
 
 // Single problem, whole grid (cooperative launch).  CG2: two classical
-// Gram-Schmidt passes per half-iteration (see fit_one).
-template <int CPT, class E, bool WARM, bool CG2 = false>
+// Gram-Schmidt passes per half-iteration; WIDE: factor products for more than
+// 128 components (see fit_one).
+template <int CPT, class E, bool WARM, bool CG2 = false, bool WIDE = false>
 __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
     __shared__ SmemFit sm;
     extern __shared__ __align__(128) unsigned char dyn_smem[];
@@ -2481,7 +2563,7 @@ __global__ void __launch_bounds__(kBlock, 1) fit_kernel(const FitArgs f) {
     ring_setup(rg, sm, dyn_smem, f.tma_stages, f.dot_groups == 2 ? 1 : PassShape<CPT>::PPR,
                f.ldp * Cell<E>::kBytes);
     unsigned epoch = 0;
-    const FitOutcome r = fit_one<CPT, E, WARM, TeamGrid, CG2>(f, tm, sm, dyn_smem, rg, threshf, epoch);
+    const FitOutcome r = fit_one<CPT, E, WARM, TeamGrid, CG2, WIDE>(f, tm, sm, dyn_smem, rg, threshf, epoch);
 #ifdef GSPCA_PHASE_TIMING
     PHASE_MARK(15);
     if (blockIdx.x == 0 && tid == 0 && f.timing)

@@ -27,6 +27,7 @@ struct Plan {
     int gs2;    // GS-PCA iterations may take the two-reduction step (see FitArgs::gs2)
     int gs_passes;  // classical Gram-Schmidt passes per half-iteration: 2 selects the CGS2 kernels
     int svd_form;   // 1: the epilogue writes the unit score directions (gspca_opts::svd_form)
+    int variant;    // kernel variant (fit_variant)
     size_t dyn;
 };
 
@@ -73,9 +74,9 @@ inline gspca_status check_opts(const gspca_opts* opts, int K) {
 // Kernel attributes and launches per (columns per thread, storage type).  They
 // are defined beside the kernels (fit_inst.cuh) and instantiated once each in
 // the fit_*.cu translation units, so the host-side units compile no kernel.
-template <int CPT, class E, bool WARM, bool CG2>
+template <int CPT, class E, bool WARM, bool CG2, bool WIDE>
 cudaError_t fit_attrs(size_t dyn, int* bps, int* static_smem);
-template <int CPT, class E, bool WARM, bool CG2>
+template <int CPT, class E, bool WARM, bool CG2, bool WIDE>
 cudaError_t launch_fit_t(const FitArgs& a, int G, size_t dyn, cudaStream_t s);
 
 // The learned warm start is compiled into the fit kernels for up to this many
@@ -89,38 +90,40 @@ template <class E>
 void launch_unpack(dim3 grid, cudaStream_t s, const void* R, int M, int N, int np, int ldp, const float* V, int ldv,
                    const float* U, int ldu, const double* lam, const int* info, int K, int gs, float* R_out);
 
-template <class E>
-inline cudaError_t fit_attrs_e(int cpt, bool warm, bool cg2, size_t dyn, int* bps, int* st) {
-    if (warm) {
-        if (cg2) return cudaErrorInvalidValue;  // no kernel has both
-        switch (cpt) {
-            case 1: return fit_attrs<1, E, true, false>(dyn, bps, st);
-            case 2: return fit_attrs<2, E, true, false>(dyn, bps, st);
-            case 4: return fit_attrs<4, E, true, false>(dyn, bps, st);
-            default: return cudaErrorInvalidValue;
-        }
-    }
-    if (cg2) {
-        switch (cpt) {
-            case 1: return fit_attrs<1, E, false, true>(dyn, bps, st);
-            case 2: return fit_attrs<2, E, false, true>(dyn, bps, st);
-            case 4: return fit_attrs<4, E, false, true>(dyn, bps, st);
-            case 8: return fit_attrs<8, E, false, true>(dyn, bps, st);
-            default: return fit_attrs<16, E, false, true>(dyn, bps, st);
-        }
-    }
+// The kernel variant of a plan: 0 plain, 1 learned warm start, 2 CGS2 (wide
+// products included), 3 wide products (more than 128 components).
+inline int fit_variant(bool warm, bool cg2, bool wide) { return warm ? 1 : cg2 ? 2 : wide ? 3 : 0; }
+
+template <class E, bool WARM, bool CG2, bool WIDE>
+inline cudaError_t fit_attrs_v(int cpt, size_t dyn, int* bps, int* st) {
     switch (cpt) {
-        case 1: return fit_attrs<1, E, false, false>(dyn, bps, st);
-        case 2: return fit_attrs<2, E, false, false>(dyn, bps, st);
-        case 4: return fit_attrs<4, E, false, false>(dyn, bps, st);
-        case 8: return fit_attrs<8, E, false, false>(dyn, bps, st);
-        default: return fit_attrs<16, E, false, false>(dyn, bps, st);
+        case 1: return fit_attrs<1, E, WARM, CG2, WIDE>(dyn, bps, st);
+        case 2: return fit_attrs<2, E, WARM, CG2, WIDE>(dyn, bps, st);
+        case 4: return fit_attrs<4, E, WARM, CG2, WIDE>(dyn, bps, st);
+        case 8: return fit_attrs<8, E, WARM, CG2, WIDE>(dyn, bps, st);
+        default: return fit_attrs<16, E, WARM, CG2, WIDE>(dyn, bps, st);
     }
 }
 
-inline cudaError_t fit_attrs_any(int cpt, int cb, bool warm, bool cg2, size_t dyn, int* bps, int* st) {
-    return cb == 8 ? fit_attrs_e<__nv_bfloat16>(cpt, warm, cg2, dyn, bps, st)
-                   : fit_attrs_e<float>(cpt, warm, cg2, dyn, bps, st);
+template <class E>
+inline cudaError_t fit_attrs_e(int cpt, int variant, size_t dyn, int* bps, int* st) {
+    switch (variant) {
+        case 1:  // learned warm start: up to 4 columns per thread
+            if (cpt > 4) return cudaErrorInvalidValue;
+            switch (cpt) {
+                case 1: return fit_attrs<1, E, true, false, false>(dyn, bps, st);
+                case 2: return fit_attrs<2, E, true, false, false>(dyn, bps, st);
+                default: return fit_attrs<4, E, true, false, false>(dyn, bps, st);
+            }
+        case 2: return fit_attrs_v<E, false, true, true>(cpt, dyn, bps, st);
+        case 3: return fit_attrs_v<E, false, false, true>(cpt, dyn, bps, st);
+        default: return fit_attrs_v<E, false, false, false>(cpt, dyn, bps, st);
+    }
+}
+
+inline cudaError_t fit_attrs_any(int cpt, int cb, int variant, size_t dyn, int* bps, int* st) {
+    return cb == 8 ? fit_attrs_e<__nv_bfloat16>(cpt, variant, dyn, bps, st)
+                   : fit_attrs_e<float>(cpt, variant, dyn, bps, st);
 }
 
 // Grid size, ring depth and shared memory for one problem.  Gcap bounds the
@@ -133,6 +136,7 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
     p->warm = opts && opts->warm;
     p->gs_passes = (opts && opts->gs_passes == 2) ? 2 : 1;
     p->svd_form = (opts && opts->svd_form == 1) ? 1 : 0;
+    p->variant = fit_variant(p->warm, p->gs_passes == 2, K > kRedundantMax);
     p->cpt = cpt_for(N);
     p->ppr = p->cpt >= 8 ? 1 : 8 / p->cpt;
     const int np = (M + 3) / 4;
@@ -174,7 +178,7 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
     cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (e != cudaSuccess) return e;
     int bps = 0, st = 0;
-    e = fit_attrs_any(p->cpt, cb, p->warm, p->gs_passes == 2, vec, &bps, &st);
+    e = fit_attrs_any(p->cpt, cb, p->variant, vec, &bps, &st);
     if (e != cudaSuccess) return e;
     const long avail = (long)optin - st - (long)vec - (long)p->res - 1024;
     // Preferred: the two-group loading pass with one panel per ring stage and an
@@ -201,38 +205,36 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
     }
     p->S = S;
     p->dyn = vec + p->res + (size_t)S * stage;
-    e = fit_attrs_any(p->cpt, cb, p->warm, p->gs_passes == 2, p->dyn, &bps, &st);
+    e = fit_attrs_any(p->cpt, cb, p->variant, p->dyn, &bps, &st);
     if (e != cudaSuccess) return e;
     if (bps < 1) return cudaErrorInvalidConfiguration;
     return cudaSuccess;
 }
 
+template <class E, bool WARM, bool CG2, bool WIDE>
+inline cudaError_t launch_fit_v(const FitArgs& a, const Plan& p, cudaStream_t s) {
+    switch (p.cpt) {
+        case 1: return launch_fit_t<1, E, WARM, CG2, WIDE>(a, p.G, p.dyn, s);
+        case 2: return launch_fit_t<2, E, WARM, CG2, WIDE>(a, p.G, p.dyn, s);
+        case 4: return launch_fit_t<4, E, WARM, CG2, WIDE>(a, p.G, p.dyn, s);
+        case 8: return launch_fit_t<8, E, WARM, CG2, WIDE>(a, p.G, p.dyn, s);
+        default: return launch_fit_t<16, E, WARM, CG2, WIDE>(a, p.G, p.dyn, s);
+    }
+}
+
 template <class E>
 inline cudaError_t launch_fit_e(const FitArgs& a, const Plan& p, cudaStream_t s) {
-    if (p.warm) {
-        if (p.gs_passes == 2) return cudaErrorInvalidValue;  // no kernel has both
-        switch (p.cpt) {
-            case 1: return launch_fit_t<1, E, true, false>(a, p.G, p.dyn, s);
-            case 2: return launch_fit_t<2, E, true, false>(a, p.G, p.dyn, s);
-            case 4: return launch_fit_t<4, E, true, false>(a, p.G, p.dyn, s);
-            default: return cudaErrorInvalidValue;
-        }
-    }
-    if (p.gs_passes == 2) {
-        switch (p.cpt) {
-            case 1: return launch_fit_t<1, E, false, true>(a, p.G, p.dyn, s);
-            case 2: return launch_fit_t<2, E, false, true>(a, p.G, p.dyn, s);
-            case 4: return launch_fit_t<4, E, false, true>(a, p.G, p.dyn, s);
-            case 8: return launch_fit_t<8, E, false, true>(a, p.G, p.dyn, s);
-            default: return launch_fit_t<16, E, false, true>(a, p.G, p.dyn, s);
-        }
-    }
-    switch (p.cpt) {
-        case 1: return launch_fit_t<1, E, false, false>(a, p.G, p.dyn, s);
-        case 2: return launch_fit_t<2, E, false, false>(a, p.G, p.dyn, s);
-        case 4: return launch_fit_t<4, E, false, false>(a, p.G, p.dyn, s);
-        case 8: return launch_fit_t<8, E, false, false>(a, p.G, p.dyn, s);
-        default: return launch_fit_t<16, E, false, false>(a, p.G, p.dyn, s);
+    switch (p.variant) {
+        case 1:
+            switch (p.cpt) {
+                case 1: return launch_fit_t<1, E, true, false, false>(a, p.G, p.dyn, s);
+                case 2: return launch_fit_t<2, E, true, false, false>(a, p.G, p.dyn, s);
+                case 4: return launch_fit_t<4, E, true, false, false>(a, p.G, p.dyn, s);
+                default: return cudaErrorInvalidValue;
+            }
+        case 2: return launch_fit_v<E, false, true, true>(a, p, s);
+        case 3: return launch_fit_v<E, false, false, true>(a, p, s);
+        default: return launch_fit_v<E, false, false, false>(a, p, s);
     }
 }
 
