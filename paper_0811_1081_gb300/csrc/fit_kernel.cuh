@@ -39,6 +39,8 @@
 // is float-float; lambda and the convergence test are FP64.
 #pragma once
 
+#include <cfloat>
+
 #include "device_common.cuh"
 #include "warmstart.cuh"
 
@@ -81,6 +83,8 @@ struct FitArgs {
     int* info;                // kInfoWords
     unsigned* flags;          // barrier arrival counter (flags[0]), zeroed before the launch
     int* abort;
+    long long* facc;          // WIDE kernels: 2 x ldk 64-bit fixed-point accumulators of b' and a'
+                              // (zeroed by the kernel itself)
     const int* iters_lock;    // device, K entries, nullable
     unsigned long long timeout_ns;
     unsigned long long* timing;  // phase-time accumulators (instrumented builds only), nullable
@@ -1001,9 +1005,9 @@ __device__ __forceinline__ void rows_times_two(const float* A, const float* B, i
 // costs one or two L2 round trips instead of one per 64 or 128 columns.  They
 // are compiled into the WIDE kernel variants only (chosen for K > 128), so the
 // kernels for fewer components keep their code and register allocation.
-template <class Y>
-__device__ __forceinline__ void rows_times_matrix_wide(const float* A, int lda, int r0, int r1, int kk, Y y,
-                                                       float* dst) {
+template <class Y, class Out>
+__device__ __forceinline__ void rows_times_matrix_wide_out(const float* A, int lda, int r0, int r1, int kk, Y y,
+                                                           Out out) {
     constexpr int RB = 16;
     const int tid = threadIdx.x, T = blockDim.x;
     for (int j0 = 0; j0 < kk; j0 += 2 * T) {
@@ -1025,10 +1029,43 @@ __device__ __forceinline__ void rows_times_matrix_wide(const float* A, int lda, 
                 sb = fmaf(b[i], yr[i], sb);
             }
         }
-        if (ja < kk) dst[ja] = sa;
-        if (jb < kk) dst[jb] = sb;
+        if (ja < kk) out(ja, sa);
+        if (jb < kk) out(jb, sb);
     }
     __syncthreads();
+}
+
+template <class Y>
+__device__ __forceinline__ void rows_times_matrix_wide(const float* A, int lda, int r0, int r1, int kk, Y y,
+                                                       float* dst) {
+    rows_times_matrix_wide_out(A, lda, r0, r1, kk, y, [&](int j, float s) { dst[j] = s; });
+}
+
+// Grid-wide sums of k-vectors without a second barrier (WIDE kernels): every
+// CTA adds its FP32 partials, scaled by 2^S and rounded to integers, into 64-bit
+// accumulators with integer atomics before the barrier that precedes their use,
+// and every CTA reads the sums after it.  Integer addition is exact and
+// independent of order, so the sums are deterministic.  S is chosen, alike in
+// every CTA, from a bound on every partial: G * bound * 2^S <= 2^61, so no sum
+// can overflow; the unit 2^-S is about 2^-52 of the bound (far below the FP32
+// rounding of the partials themselves).
+// S from two factors of the bound, a and b (G a b < 2^e), in integer and FP32
+// arithmetic only (GB300 runs FP64 at a small fraction of the FP32 rate).
+__device__ __forceinline__ int fx_shift(float a, float b, int G) {
+    const int e = (32 - __clz(G)) + ilogbf(fmaxf(a, FLT_MIN)) + 1 + ilogbf(fmaxf(b, FLT_MIN)) + 1;
+    return 61 - e;
+}
+
+__device__ __forceinline__ void fx_add(long long* acc, float x, int S, int G) {
+    const float lim = ldexpf(1.f, 61 - (32 - __clz(G)));  // 2^61 / G or less
+    float y = ldexpf(x, S);  // exact: a power-of-two scaling within the FP32 range
+    if (!(y == y)) y = 0.f;  // NaN (a failed pass): the degenerate test catches it
+    y = fminf(fmaxf(y, -lim), lim);
+    atomicAdd(reinterpret_cast<unsigned long long*>(acc), (unsigned long long)__float2ll_rn(y));
+}
+
+__device__ __forceinline__ float fx_get(const long long* acc, int S) {
+    return ldexpf(__ll2float_rn(__ldcg(acc)), -S);
 }
 
 template <class Pre, class Fn>
@@ -1969,6 +2006,11 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
         __syncthreads();
     }
     double lam0 = 0.0;  // lambda of component 0 (the two-reduction step's range guard)
+    // WIDE: ||X||_F for the bounds of the fixed-point sums; the accumulators start at zero
+    // (this CTA's share; the first barrier orders the stores before any use)
+    const float xnorm = WIDE ? (float)sqrt(sm.dsc[0]) : 0.f;
+    if constexpr (WIDE)
+        for (int i = g * T + tid; i < 2 * f.ldk; i += G * T) f.facc[i] = 0;
 
     int status = kStOK, found = K;
     long long total = 0;
@@ -2295,10 +2337,32 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
             // (lambda_0 <= 64 mu): there Q and Z track R_k U and U^T W to the accuracy of the
             // direct products.  Every CTA decides alike from the same reduced values.
             const bool try2 = gs2 && gs && k > 0 && mu.hi > 0.f && (float)lam0 <= 64.f * mu.hi;
-            if (try2)  // b' = V_(k)^T v' and c' = Q^T v' = U^T s' over this CTA's rows
+            // WIDE past 128 components: b' and a' through the fixed-point accumulators
+            const bool fxk = WIDE && gs && k > f.redundant_max;
+            int fx_b = 0, fx_a = 0;  // scale exponents S of the b' and a' sums
+            if (try2) {  // b' = V_(k)^T v' and c' = Q^T v' = U^T s' over this CTA's rows
                 rows_times_two(Vl, Ql, f.ldv, r0, r1, k, [&](int r) { return f.vraw[r]; }, pA + N, pA + N + k, sm);
-            else if (gs && k > 0)  // b' = V_(k)^T v' over this CTA's rows
+            } else if (fxk) {
+                // |b'_j| over any rows <= ||v'|| <= ||R||_F ||u'|| <= ||X||_F ||u'||: ||u'||^2 from the
+                // CTA partials of the last loading (every CTA alike), a factor 4 to spare
+                if (warp == 0) {
+                    ff a = ff_zero();
+                    for (int i = lane; i < G; i += 32) {
+                        const float2 q = ldcg(f.spart + (size_t)i * 4 + 2 + buf);
+                        a = ff_add(a, ff{q.x, q.y});
+                    }
+                    a = warp_sum_ff(a);
+                    if (lane == 0) sm.tmpf[0][0] = __fadd_rn(a.hi, a.lo);
+                }
+                // a' of the last iteration was read before the last barrier: clear its accumulators
+                for (int i = g * T + tid; i < k; i += G * T) f.facc[f.ldk + i] = 0;
+                __syncthreads();
+                fx_b = fx_shift(4.f * xnorm, sqrtf(fmaxf(sm.tmpf[0][0], 0.f)), G);
+                rows_times_matrix_wide_out(Vl, f.ldv, r0, r1, k, [&](int r) { return f.vraw[r]; },
+                                           [&](int jj, float s) { fx_add(f.facc + jj, s, fx_b, G); });
+            } else if (gs && k > 0) {  // b' = V_(k)^T v' over this CTA's rows
                 rows_times_matrix<kWide>(Vl, f.ldv, r0, r1, k, [&](int r) { return f.vraw[r]; }, pA + N, sm);
+            }
             PHASE_MARK(3);
             GS_SYNC();
             PHASE_MARK(4);
@@ -2329,7 +2393,10 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
             } else {
                 // b' -> kb; v_corr' = v' - V b' (rows); u_pre' = s' - W b' (slice);
                 // a' = U^T u_pre' (partials)
-                if (!small_k) {
+                if (fxk) {
+                    for (int jj = tid; jj < k; jj += T) kb[jj] = fx_get(f.facc + jj, fx_b);
+                    __syncthreads();
+                } else if (!small_k) {
                     reduce_cols_distributed(f.partA, G, g, f.LA, N, k, f.red);
                     GS_SYNC();
                     for (int jj = tid; jj < k; jj += T) kb[jj] = (float)ldcg(f.red + jj);
@@ -2405,7 +2472,15 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                         Wl, f.ldw, n0, n1, k, kb, [&](int n) { return sv[n - n0]; },
                         [&](int n, float s, float p) { f.upre[n] = p - s; });
                     __syncthreads();
-                    rows_times_matrix<kWide>(Ul, f.ldu, n0, n1, k, [&](int n) { return f.upre[n]; }, pB, sm);
+                    if (fxk) {
+                        // |a'_j| over any slice <= ||u_pre'|| <= ||R||_F ||v' - V b'|| <= 2 ||X||_F ||v'||,
+                        // a factor 4 to spare
+                        fx_a = fx_shift(8.f * xnorm, sqrtf(fmaxf(__fadd_rn(nvp.hi, nvp.lo), 0.f)), G);
+                        rows_times_matrix_wide_out(Ul, f.ldu, n0, n1, k, [&](int n) { return f.upre[n]; },
+                                                   [&](int jj, float s) { fx_add(f.facc + f.ldk + jj, s, fx_a, G); });
+                    } else {
+                        rows_times_matrix<kWide>(Ul, f.ldu, n0, n1, k, [&](int n) { return f.upre[n]; }, pB, sm);
+                    }
                     l2 = block_sum_ff(l2, sm);
                     write_scalar(f, g, 1, l2);
                     PHASE_MARK(7);
@@ -2413,7 +2488,12 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                     PHASE_MARK(8);
                     gather_reduce(f, sm, G, 1, 1, 0, f.partB, f.LB, small_k ? k : 0, ident, ka);
                     lam2p = sm.sff[0];
-                    if (!small_k) {
+                    if (fxk) {
+                        for (int jj = tid; jj < k; jj += T) ka[jj] = fx_get(f.facc + f.ldk + jj, fx_a);
+                        // every CTA read b' before this barrier: clear its accumulators (this CTA's share)
+                        for (int i = g * T + tid; i < k; i += G * T) f.facc[i] = 0;
+                        __syncthreads();
+                    } else if (!small_k) {
                         reduce_cols_distributed(f.partB, G, g, f.LB, 0, k, f.red);
                         GS_SYNC();
                         for (int jj = tid; jj < k; jj += T) ka[jj] = (float)ldcg(f.red + jj);

@@ -279,6 +279,7 @@ inline FitArgs make_args(const Workspace& w, const Plan& p, int M, int N, int K,
     a.info = w.info;
     a.flags = w.flags;
     a.abort = w.abort;
+    a.facc = w.facc;
     a.iters_lock = lock_dev;
     a.timeout_ns = (unsigned long long)(timeout_s * 1e9);
     a.timing = nullptr;

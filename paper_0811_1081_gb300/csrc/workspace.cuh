@@ -38,6 +38,7 @@ struct Workspace {
     double *red, *lam, *xpart, *cmean, *rmean;
     int *iters, *info, *abort, *lock;
     unsigned* flags;
+    long long* facc;  // 2 x ld fixed-point accumulators (kernels for more than 128 components)
     int ld, LA, LB, G, xcap;
     size_t bytes;
 };
@@ -79,6 +80,7 @@ inline Workspace carve(void* base, const WsDims& d) {
     w.abort = (int*)take(sizeof(int) * 4);
     w.lock = (int*)take(sizeof(int) * (size_t)d.K);
     w.flags = (unsigned*)take(sizeof(unsigned) * 32);
+    w.facc = (long long*)take(sizeof(long long) * 2 * (size_t)w.ld);
     if (d.warm) {
         w.wsF = (float*)take(sizeof(float) * 17 * (size_t)d.N);
         w.wsP0 = (float*)take(sizeof(float) * (size_t)d.N);
