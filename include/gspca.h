@@ -149,6 +149,14 @@ typedef struct {
                                V(k) for GS-PCA, t_k / lambda_k for NIPALS-PCA.  With K = N and every
                                component converged, R vanishes and (T, lambda, P) is the full SVD.
                                The batched entry points accept 0 only (GSPCA_ERR_NOT_SUPPORTED). */
+    float *coef_trace;      /* testing aid, nullable; gspca_fit only (device pointer, ignored by the
+                               other entry points): K * (2K + M + N) floats.  For every GS-PCA
+                               component k >= 1 the last iteration's Gram-Schmidt coefficients
+                               b' = V_(k)^T v' (floats [k(2K+M+N), +k)) and a' = U_(k)^T u_pre'
+                               ([k(2K+M+N) + K, +k)), and the vectors they were formed from: v' = R u'
+                               (M floats from k(2K+M+N) + 2K) and u_pre' = R^T (v' - V_(k) b')
+                               (N floats after v'), both in the pass's scale.  Other entries are
+                               left untouched. */
 } gspca_opts;
 
 /* Per-call record of the last fit on a handle (host memory). */

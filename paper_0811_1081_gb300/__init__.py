@@ -59,7 +59,8 @@ class Opts(ctypes.Structure):
                 ("grid_ctas", ctypes.c_int), ("timeout_s", ctypes.c_double),
                 ("cluster_ctas", ctypes.c_int), ("batch_pass", ctypes.c_int), ("test_stall", ctypes.c_int),
                 ("warm", ctypes.POINTER(WarmStartC)), ("resident", ctypes.c_int), ("load_path", ctypes.c_int),
-                ("gs_step", ctypes.c_int), ("gs_passes", ctypes.c_int), ("svd_form", ctypes.c_int)]
+                ("gs_step", ctypes.c_int), ("gs_passes", ctypes.c_int), ("svd_form", ctypes.c_int),
+                ("coef_trace", ctypes.c_void_p)]
 
 
 class Info(ctypes.Structure):
@@ -150,8 +151,9 @@ class WarmStart:
 
 
 def _opts(center=0, iters_lock=None, grid_ctas=0, timeout_s=0.0, cluster_ctas=0, test_stall=0, batch_pass=0,
-          warm=None, resident=0, load_path=0, gs_step=0, gs_passes=0, svd_form=0):
+          warm=None, resident=0, load_path=0, gs_step=0, gs_passes=0, svd_form=0, coef_trace=None):
     o = Opts()
+    o.coef_trace = coef_trace.data_ptr() if coef_trace is not None else None
     o.gs_passes = int(gs_passes)
     o.svd_form = int(svd_form)
     o.resident = int(resident)
@@ -222,11 +224,12 @@ def gspca_fit(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="
               center: int = 0, iters_lock=None, want_R: bool = False, grid_ctas: int = 0,
               timeout_s: float = 0.0, stream=None, check: bool = True, test_stall: int = 0,
               warm: WarmStart | None = None, resident: int = 0, load_path: int = 0,
-              gs_step: int = 0, gs_passes: int = 0, svd_form: int = 0) -> FitResult:
+              gs_step: int = 0, gs_passes: int = 0, svd_form: int = 0, coef_trace=None) -> FitResult:
     """Fit K components of X (a float32 CUDA tensor, any 2-D strided layout).  `warm`: the
     learned warm start (GS-PCA); the result's ws_choice marks the components that used it.
     `gs_passes=2`: two classical Gram-Schmidt passes per half-iteration (CGS2).
-    `svd_form=1`: T receives the unit score directions (X = T diag(lam) P^T + R)."""
+    `svd_form=1`: T receives the unit score directions (X = T diag(lam) P^T + R).
+    `coef_trace` (testing aid): a float32 CUDA tensor of K * (2K + M + N) values, see gspca.h."""
     import torch
 
     if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
@@ -247,7 +250,8 @@ def gspca_fit(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="
     choice = torch.zeros(K, device=dev, dtype=torch.int32) if warm is not None else None
     o, keep = _opts(center, iters_lock, grid_ctas, timeout_s, 0, test_stall,
                     warm=warm.c_struct(choice) if warm is not None else None, resident=resident,
-                    load_path=load_path, gs_step=gs_step, gs_passes=gs_passes, svd_form=svd_form)
+                    load_path=load_path, gs_step=gs_step, gs_passes=gs_passes, svd_form=svd_form,
+                    coef_trace=coef_trace)
     st = load().gspca_fit(ctypes.c_void_p(h), ctypes.c_void_p(stream), ctypes.c_void_p(X.data_ptr()),
                           layout, int(ldx), M, N, int(K), float(tol), int(max_iter), _ALGOS[algo],
                           ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(P.data_ptr()),

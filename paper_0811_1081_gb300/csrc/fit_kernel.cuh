@@ -85,6 +85,8 @@ struct FitArgs {
     int* abort;
     long long* facc;          // WIDE kernels: 2 x ldk 64-bit fixed-point accumulators of b' and a'
                               // (zeroed by the kernel itself)
+    float* coef_trace;        // testing aid, nullable: per component k >= 1, at k (2K + M + N), the
+                              // last iteration's b' (K slots), a' (K slots), v' (M) and u_pre' (N)
     const int* iters_lock;    // device, K entries, nullable
     unsigned long long timeout_ns;
     unsigned long long* timing;  // phase-time accumulators (instrumented builds only), nullable
@@ -2565,6 +2567,16 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                         Vl, f.ldv, r0, r1, k, kb, [&](int r) { return ldcg(f.vraw + r); },
                         [&](int r, float s, float p) { f.vcorr[r] = p - s; });
                     __syncthreads();
+                }
+                if (f.coef_trace != nullptr && gs && k > 0) {
+                    float* tr = f.coef_trace + (size_t)k * (2 * K + f.M + N);
+                    if (g == 0)
+                        for (int i = tid; i < k; i += T) {
+                            tr[i] = kb[i];
+                            tr[K + i] = ka[i];
+                        }
+                    for (int r = r0 + tid; r < r1; r += T) tr[2 * K + r] = ldcg(f.vraw + r);
+                    for (int n = n0 + tid; n < n1; n += T) tr[2 * K + f.M + n] = ldcg(f.upre + n);
                 }
                 const float vinv = __fdiv_rn(1.f, __fsqrt_rn(l2f));
                 const bool res = f.res_rows > 0;

@@ -106,6 +106,7 @@ gspca_status enqueue_fit(gspca_t h, cudaStream_t s, const float* X, gspca_layout
     }
     FitArgs a = make_args(h->ws, plan, M, N, K, tol, max_iter, algo, lock_dev, timeout, nxpart);
     if (opts && opts->test_stall) a.stall_word = h->ws.abort + 2;  // a word nothing sets
+    if (opts) a.coef_trace = opts->coef_trace;
     if (warm) {
         a.ws_net = warm->net;
         a.ws_G = warm->G;
