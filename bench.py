@@ -79,22 +79,40 @@ def source_sha():
     return hsh.hexdigest()
 
 
-def profiled_traffic(kernel, workload):
-    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary
-    (profiles/<kernel>_<workload>.md), or None when it is absent or was taken on other sources."""
+def profile_values(kernel, workload):
+    """The "- key: value" figures of the committed ncu summary profiles/<kernel>_<workload>.md
+    ({} when absent), and whether it was taken on the current sources."""
     p = os.path.join(ROOT, "profiles", f"{profile_stem(kernel)}_{workload}.md")
     if not os.path.exists(p):
-        return None, None
+        return {}, False, None
     vals = {}
     with open(p) as f:
         for ln in f:
             if ":" in ln and ln.strip().startswith("- "):
                 k, v = ln.strip()[2:].split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
-    if vals.get("source_sha256") != source_sha():
+    return vals, vals.get("source_sha256") == source_sha(), p
+
+
+def profiled_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary, or None
+    when it is absent or was taken on other sources."""
+    vals, fresh, p = profile_values(kernel, workload)
+    if not fresh:
         return None, p
     try:
         return float(vals["dram_bytes_per_launch"]), p
+    except (KeyError, ValueError):
+        return None, p
+
+
+def l2_read_peak(kernel, workload):
+    """Peak L2 -> SM read bandwidth (GB/s) of this GPU from an ncu capture: the bytes read by the
+    SMs from L2 per second divided by ncu's percentage of their sustained peak (a property of the
+    hardware and its clocks, so it is used whatever the sources); None without a capture."""
+    vals, _, p = profile_values(kernel, workload)
+    try:
+        return float(vals["l2_read_peak_gbs"]), p
     except (KeyError, ValueError):
         return None, p
 
@@ -106,38 +124,6 @@ def measured_peaks():
             d = json.load(f)
         return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
     return FALLBACK_HBM_GBS, "fallback"
-
-
-def measure_l2_peak(dev, nbytes=80_000_000, reps=30):
-    """Streaming bandwidth of data that stays in L2 (no flush between repetitions): the
-    best of `reps` CUDA-event-timed runs of a read-only reduction (x.sum()) over nbytes and
-    of a copy between two nbytes/2 buffers (read + write bytes).  These are PyTorch's
-    kernels, not this library's: the denominator for a kernel whose R stays in L2."""
-    import torch
-
-    x = torch.ones(nbytes // 4, dtype=torch.float32, device=dev)
-    a = torch.ones(nbytes // 8, dtype=torch.float32, device=dev)
-    b = torch.empty_like(a)
-    st = torch.cuda.current_stream(dev)
-
-    def best(fn, nb):
-        for _ in range(5):
-            fn()
-        ms = []
-        for _ in range(reps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            fn()
-            e1.record(st)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        return nb / (min(ms) / 1e3) / 1e9
-
-    read = best(lambda: x.sum(), nbytes)
-    copy = best(lambda: b.copy_(a), nbytes)
-    del x, a, b
-    return {"gbs": max(read, copy), "read_gbs": read, "copy_gbs": copy, "buffer_bytes": nbytes,
-            "how": "best of 30 L2-resident runs each of torch x.sum() (80 MB) and b.copy_(a) (2 x 40 MB)"}
 
 
 class ClockSampler:
@@ -621,8 +607,10 @@ def main():
     else:
         bound = "l2" if r_bytes <= 0.75 * l2_size else "hbm"
         bound_basis = f"R {r_bytes / 1e6:.0f} MB vs L2 {l2_size / 1e6:.0f} MB (l2 up to 75%)"
-    l2pk = measure_l2_peak(dev)
-    rpeak = l2pk["gbs"] if bound == "l2" else peak
+    l2pk, l2src = l2_read_peak(kname, w.name)
+    if bound == "l2" and l2pk is None:
+        bound, bound_basis = "hbm", bound_basis + "; no L2 peak recorded, HBM peak used"
+    rpeak = l2pk if bound == "l2" else peak
 
     # end to end through the host-buffer entry point (pinned host memory)
     Xh = torch.from_numpy(X32).pin_memory()
@@ -658,9 +646,10 @@ def main():
         "roofline": {"bound": bound, "achieved": achieved, "peak": rpeak, "unit": "GB/s",
                      "frac": achieved / rpeak, "traffic": traffic, "kernel": kname,
                      "bound_basis": bound_basis,
-                     "peak_source": ("measured in this run: " + l2pk["how"]) if bound == "l2"
+                     "peak_source": (f"ncu L2->SM read peak (l1tex__m_xbar2l1tex_read_bytes per second / pct of "
+                                     f"peak sustained), {os.path.relpath(l2src, ROOT)}") if bound == "l2"
                      else f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
-                     "hbm_peak": peak, "frac_of_hbm_peak": achieved / peak, "l2_peak": l2pk,
+                     "hbm_peak": peak, "frac_of_hbm_peak": achieved / peak,
                      "traffic_source": traffic_src, "kernel_share_of_step": kernel_share,
                      "kernel_ms_mean": statistics.mean(kern_ms),
                      "alg_bytes_per_launch": alg_launch},
