@@ -47,11 +47,15 @@ typedef struct gspca_handle *gspca_t;
 
 typedef enum { GSPCA_NIPALS = 0, GSPCA_GS = 1 } gspca_algo;
 
-/* Storage type of the residual R inside the library (X is always FP32).
- * GSPCA_BF16: X is rounded to bfloat16 once; every product uses FP32
- * accumulation and the Gram-Schmidt coefficients, norms and the test stay in
- * FP64-combined FP32 sums. */
-typedef enum { GSPCA_F32 = 0, GSPCA_BF16 = 1 } gspca_dtype;
+/* Storage type of the residual R inside the library.
+ * GSPCA_F32, GSPCA_BF16: X is FP32 (gspca_fit and the other entry points);
+ *   GSPCA_BF16 rounds X to bfloat16 once; every product uses FP32 accumulation
+ *   and the Gram-Schmidt coefficients, norms and the test stay in float-float /
+ *   FP64-combined FP32 sums.
+ * GSPCA_F64: the paper's own precision (Sec. 3): X, R, the factors, every
+ *   product, the outputs and the test in IEEE double; only gspca_fit_f64 takes
+ *   such a handle. */
+typedef enum { GSPCA_F32 = 0, GSPCA_BF16 = 1, GSPCA_F64 = 2 } gspca_dtype;
 
 typedef enum { GSPCA_COL_MAJOR = 0, GSPCA_ROW_MAJOR = 1 } gspca_layout;
 
@@ -187,8 +191,9 @@ gspca_status gspca_create(gspca_t *h, int device, long max_M, long max_N, int ma
  * Sec. 2.2 / 2.3 pseudo-code with a device-resident loop: one persistent
  * kernel runs every iteration and every convergence decision; the host only
  * enqueues it and, at the end, synchronises `stream` and reads the status.
- * Requirements: 1 <= K <= min(M, N), M <= max_M, N <= max_N, K <= max_K,
- * tol > 0, max_iter >= 1, T, P, lambda non-NULL; iters, R_out, opts nullable.
+ * Requirements: a GSPCA_F32 or GSPCA_BF16 handle, 1 <= K <= min(M, N),
+ * M <= max_M, N <= max_N, K <= max_K, tol > 0, max_iter >= 1, T, P, lambda
+ * non-NULL; iters, R_out, opts nullable.
  * Returns GSPCA_OK, GSPCA_WARN_NOT_CONVERGED or GSPCA_ERR_DEGENERATE with valid
  * outputs; other codes leave the outputs unspecified. */
 gspca_status gspca_fit(gspca_t h, void *stream, const float *X, gspca_layout layout, long ldx,
@@ -205,6 +210,21 @@ gspca_status gspca_fit_host(gspca_t h, void *stream, const float *X, gspca_layou
                             long ldx, int M, int N, int K, double tol, int max_iter,
                             gspca_algo algo, float *T, float *P, double *lambda, int *iters,
                             float *R_out, const gspca_opts *opts);
+
+/* Fit in FP64 (the precision of the paper's programs, Sec. 3): NIPALS-PCA or
+ * GS-PCA (Sec. 2.2 / 2.3) with X, R, the factors, every product and sum, the
+ * outputs and the convergence test in IEEE double, on a handle created with
+ * GSPCA_F64.  Same arguments and conventions as gspca_fit with double for X, T,
+ * P and R_out (device pointers).  Cross-CTA sums run in a fixed order, so two
+ * runs give the same bits; the results match an FP64 evaluation in another
+ * summation order to rounding.  opts: center, iters_lock, grid_ctas, timeout_s
+ * and svd_form apply; warm, gs_passes = 2 and coef_trace give
+ * GSPCA_ERR_NOT_SUPPORTED.  Also GSPCA_ERR_INVALID_ARG for a handle of another
+ * dtype, GSPCA_ERR_NOT_SUPPORTED when one row of N doubles (and the loop's
+ * vectors) does not fit a CTA's shared memory (about N > 8192). */
+gspca_status gspca_fit_f64(gspca_t h, void *stream, const double *X, gspca_layout layout, long ldx, int M, int N,
+                           int K, double tol, int max_iter, gspca_algo algo, double *T, double *P, double *lambda,
+                           int *iters, double *R_out, const gspca_opts *opts);
 
 /* One independent problem of a batch (device pointers, same conventions as
  * gspca_fit, column-major X with leading dimension ldx). */

@@ -18,7 +18,7 @@ from dataclasses import dataclass
 from .buildlib import LIB, build
 
 GSPCA_NIPALS, GSPCA_GS = 0, 1
-GSPCA_F32, GSPCA_BF16 = 0, 1
+GSPCA_F32, GSPCA_BF16, GSPCA_F64 = 0, 1, 2
 GSPCA_COL_MAJOR, GSPCA_ROW_MAJOR = 0, 1
 GSPCA_CENTER_NONE, GSPCA_CENTER_COLUMNS, GSPCA_CENTER_ROWS = 0, 1, 2
 GSPCA_OK = 0
@@ -32,12 +32,13 @@ GSPCA_ERR_NOT_SUPPORTED = 7
 
 EXPORTS = ["gspca_create", "gspca_fit", "gspca_fit_host", "gspca_fit_batched", "gspca_fit_batched_async",
            "gspca_get_info", "gspca_destroy", "gspca_status_string", "gspca_last_cuda_error",
-           "gspca_fit_noalloc", "gspca_ws_features", "gspca_ws_forward", "gspca_ws_train_step"]
+           "gspca_fit_noalloc", "gspca_ws_features", "gspca_ws_forward", "gspca_ws_train_step", "gspca_fit_f64"]
 
 WS_SKETCH, WS_FEATURES, WS_PARAMS = 16, 17, 5377
 
 _ALGOS = {"nipals": GSPCA_NIPALS, "gs": GSPCA_GS, GSPCA_NIPALS: GSPCA_NIPALS, GSPCA_GS: GSPCA_GS}
-_DTYPES = {"f32": GSPCA_F32, "bf16": GSPCA_BF16, GSPCA_F32: GSPCA_F32, GSPCA_BF16: GSPCA_BF16}
+_DTYPES = {"f32": GSPCA_F32, "bf16": GSPCA_BF16, "f64": GSPCA_F64, GSPCA_F32: GSPCA_F32, GSPCA_BF16: GSPCA_BF16,
+           GSPCA_F64: GSPCA_F64}
 
 
 class GspcaError(RuntimeError):
@@ -97,6 +98,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.gspca_fit_host.argtypes = fit_args
     lib.gspca_fit_batched.argtypes = [vp, vp, ctypes.POINTER(Problem), i, d, i, i, ctypes.POINTER(Opts)]
     lib.gspca_fit_batched_async.argtypes = [vp, vp, ctypes.POINTER(Problem), i, d, i, i, ctypes.POINTER(Opts), vp]
+    lib.gspca_fit_f64.argtypes = fit_args
     lib.gspca_fit_noalloc.argtypes = fit_args[1:]
     lib.gspca_fit_noalloc.restype = i
     lib.gspca_ws_features.argtypes = [vp, vp, l, i, i, vp, vp, i, vp, vp]
@@ -109,7 +111,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.gspca_last_cuda_error.argtypes = []
     lib.gspca_last_cuda_error.restype = ctypes.c_char_p
     for name in ("gspca_create", "gspca_fit", "gspca_fit_host", "gspca_fit_batched",
-                 "gspca_fit_batched_async", "gspca_get_info", "gspca_destroy", "gspca_ws_features",
+                 "gspca_fit_batched_async", "gspca_get_info", "gspca_destroy", "gspca_ws_features", "gspca_fit_f64",
                  "gspca_ws_forward", "gspca_ws_train_step"):
         getattr(lib, name).restype = i
     _lib = lib
@@ -263,6 +265,40 @@ def gspca_fit(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="
     return FitResult(T, P, lam, iters, R, st, gspca_get_info(h), choice)
 
 
+def gspca_fit_f64(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="gs", center: int = 0,
+                  iters_lock=None, want_R: bool = False, grid_ctas: int = 0, timeout_s: float = 0.0, stream=None,
+                  check: bool = True, svd_form: int = 0) -> FitResult:
+    """FP64 fit on a handle created with dtype="f64": X a 2-D float64 CUDA tensor (any row- or
+    column-major strides); T, P, lam and R are float64."""
+    import torch
+
+    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float64 and X.dim() == 2):
+        raise TypeError("X must be a 2-D float64 CUDA tensor")
+    layout, ldx = _layout_of(X)
+    if layout is None:
+        X = X.contiguous()
+        layout, ldx = GSPCA_ROW_MAJOR, X.shape[1]
+    M, N = X.shape
+    dev = X.device
+    T = torch.empty((K, M), device=dev, dtype=torch.float64).t()
+    P = torch.empty((K, N), device=dev, dtype=torch.float64).t()
+    lam = torch.empty(K, device=dev, dtype=torch.float64)
+    iters = torch.empty(K, device=dev, dtype=torch.int32)
+    R = torch.empty((N, M), device=dev, dtype=torch.float64).t() if want_R else None
+    if stream is None:
+        stream = torch.cuda.current_stream(dev).cuda_stream
+    o, keep = _opts(center, iters_lock, grid_ctas, timeout_s, svd_form=svd_form)
+    st = load().gspca_fit_f64(ctypes.c_void_p(h), ctypes.c_void_p(stream), ctypes.c_void_p(X.data_ptr()), layout,
+                              int(ldx), M, N, int(K), float(tol), int(max_iter), _ALGOS[algo],
+                              ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(P.data_ptr()),
+                              ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(iters.data_ptr()),
+                              ctypes.c_void_p(R.data_ptr()) if R is not None else None, ctypes.byref(o))
+    del keep
+    if check and st not in (GSPCA_OK, GSPCA_WARN_NOT_CONVERGED, GSPCA_ERR_DEGENERATE):
+        raise GspcaError(st, "gspca_fit_f64")
+    return FitResult(T, P, lam, iters, R, st, gspca_get_info(h))
+
+
 def gspca_fit_host(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="gs",
                    center: int = 0, iters_lock=None, want_R: bool = False, stream=None,
                    out=None, check: bool = True, gs_passes: int = 0, svd_form: int = 0) -> FitResult:
@@ -320,6 +356,9 @@ class Handle:
 
     def fit_host(self, X, K, **kw) -> FitResult:
         return gspca_fit_host(self.h, X, K, **kw)
+
+    def fit64(self, X, K, **kw) -> FitResult:
+        return gspca_fit_f64(self.h, X, K, **kw)
 
     def info(self) -> dict:
         return gspca_get_info(self.h)

@@ -113,6 +113,7 @@ uint64_t shape_key(const gspca_problem* p, int count, int algo, bool warm) {
 gspca_status check_batch(gspca_t h, const gspca_problem* p, int count, double tol, int max_iter, gspca_algo algo,
                          const gspca_opts* opts) {
     if (!h || !p || count < 1 || !(tol > 0.0) || max_iter < 1) return GSPCA_ERR_INVALID_ARG;
+    if (h->dtype == GSPCA_F64) return GSPCA_ERR_NOT_SUPPORTED;  // the batched kernel stores R as FP32 or BF16
     if (algo != GSPCA_NIPALS && algo != GSPCA_GS) return GSPCA_ERR_INVALID_ARG;
     if (count > kBatchMax * kBatchChunks) return GSPCA_ERR_NOT_SUPPORTED;
     if (opts) {

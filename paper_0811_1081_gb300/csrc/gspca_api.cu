@@ -36,6 +36,7 @@ gspca_status check_fit_args(gspca_t h, const void* X, gspca_layout layout, long 
                             double tol, int max_iter, gspca_algo algo, const void* T, const void* P,
                             const void* lambda, const gspca_opts* opts) {
     if (!h || !X || !T || !P || !lambda) return GSPCA_ERR_INVALID_ARG;
+    if (h->dtype == GSPCA_F64) return GSPCA_ERR_INVALID_ARG;  // FP64 handles take gspca_fit_f64
     if (M < 1 || N < 1 || K < 1 || K > M || K > N) return GSPCA_ERR_INVALID_ARG;
     if (M > h->max_M || N > h->max_N || K > h->max_K) return GSPCA_ERR_INVALID_ARG;
     if (!(tol > 0.0) || max_iter < 1) return GSPCA_ERR_INVALID_ARG;
@@ -188,7 +189,7 @@ gspca_status gspca_create(gspca_t* out, int device, long max_M, long max_N, int 
     if (!out) return GSPCA_ERR_INVALID_ARG;
     *out = nullptr;
     if (max_M < 1 || max_N < 1 || max_K < 1 || max_K > max_N || max_K > max_M) return GSPCA_ERR_INVALID_ARG;
-    if (dtype != GSPCA_F32 && dtype != GSPCA_BF16) return GSPCA_ERR_INVALID_ARG;
+    if (dtype != GSPCA_F32 && dtype != GSPCA_BF16 && dtype != GSPCA_F64) return GSPCA_ERR_INVALID_ARG;
     if (max_N > kMaxCols) return GSPCA_ERR_NOT_SUPPORTED;
     GS_CUDA(cudaSetDevice(device));
     gspca_handle* h = new (std::nothrow) gspca_handle();
@@ -202,22 +203,33 @@ gspca_status gspca_create(gspca_t* out, int device, long max_M, long max_N, int 
         delete h;
         return GSPCA_ERR_CUDA;
     }
+    if (!cuda_ok(cudaMallocHost((void**)&h->h_info, sizeof(int) * (kInfoWords + 4 + (size_t)max_K))) ||
+        !cuda_ok(cudaEventCreate(&h->ev0)) || !cuda_ok(cudaEventCreate(&h->ev1))) {
+        gspca_destroy(h);
+        return GSPCA_ERR_CUDA;
+    }
+    if (dtype == GSPCA_F64) {  // the FP64 storage path has a workspace of its own
+        const gspca_status st = create_ws64(h);
+        if (st != GSPCA_OK) {
+            gspca_destroy(h);
+            return st;
+        }
+        *out = h;
+        return GSPCA_OK;
+    }
     const WsDims dims{(max_M + 3) / 4 * 4, (int)max_N, max_K, h->num_sms};
     const Workspace probe = carve(nullptr, dims);
     void* base = nullptr;
     cudaError_t e = cudaMalloc(&base, probe.bytes);
     if (e != cudaSuccess) {
         cuda_ok(e);
-        delete h;
+        gspca_destroy(h);
         return e == cudaErrorMemoryAllocation ? GSPCA_ERR_OOM : GSPCA_ERR_CUDA;
     }
     h->ws_base = base;
     h->ws = carve(base, dims);
-    if (!cuda_ok(cudaMemset(base, 0, probe.bytes)) ||
-        !cuda_ok(cudaMallocHost((void**)&h->h_info, sizeof(int) * (kInfoWords + 4 + (size_t)max_K))) ||
-        !cuda_ok(cudaEventCreate(&h->ev0)) || !cuda_ok(cudaEventCreate(&h->ev1))) {
-        cudaFree(base);
-        delete h;
+    if (!cuda_ok(cudaMemset(base, 0, probe.bytes))) {
+        gspca_destroy(h);
         return GSPCA_ERR_CUDA;
     }
     *out = h;
@@ -302,6 +314,7 @@ gspca_status gspca_destroy(gspca_t h) {
     gspca_status st = GSPCA_OK;
     if (h->stage && !cuda_ok(cudaFree(h->stage))) st = GSPCA_ERR_CUDA;
     if (h->ws_base && !cuda_ok(cudaFree(h->ws_base))) st = GSPCA_ERR_CUDA;
+    if (h->ws64_base && !cuda_ok(cudaFree(h->ws64_base))) st = GSPCA_ERR_CUDA;
     if (h->ws_train && !cuda_ok(cudaFree(h->ws_train))) st = GSPCA_ERR_CUDA;
     if (h->h_info && !cuda_ok(cudaFreeHost(h->h_info))) st = GSPCA_ERR_CUDA;
     if (h->ev0) cudaEventDestroy(h->ev0);

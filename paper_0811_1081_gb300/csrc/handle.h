@@ -9,6 +9,7 @@
 
 #include "../../include/gspca.h"
 #include "workspace.cuh"
+#include "workspace64.cuh"
 
 namespace gspca {
 
@@ -44,6 +45,13 @@ void batch_release(BatchState& b);
 
 }  // namespace gspca
 
+struct gspca_handle;
+
+namespace gspca {
+// Allocate the FP64 workspace of a GSPCA_F64 handle (fit64_api.cu).
+gspca_status create_ws64(gspca_handle* h);
+}  // namespace gspca
+
 #define GS_CUDA(call)                                     \
     do {                                                  \
         if (!gspca::cuda_ok(call)) return GSPCA_ERR_CUDA; \
@@ -68,4 +76,6 @@ struct gspca_handle {
     gspca::BatchState batch;
     void* ws_train = nullptr;       // scratch of gspca_ws_train_step (grown on demand)
     size_t ws_train_bytes = 0;
+    void* ws64_base = nullptr;      // GSPCA_F64 handles: the FP64 workspace (instead of ws)
+    gspca::Workspace64 ws64{};
 };
