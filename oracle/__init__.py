@@ -77,6 +77,9 @@ def _bind(lib):
                                ctypes.c_int, dp, dp, ip, dp, dp, dp, dp, ip, dp, ip]
     lib.oracle_cgs.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int]
     lib.oracle_cgs.restype = ctypes.c_int
+    lib.oracle_block_fit.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_int, ip, dp, dp, dp, ip, dp, ip]
+    lib.oracle_block_fit.restype = ctypes.c_int
     lib.oracle_ws_nparams.restype = ctypes.c_int
     lib.oracle_ws_features.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp]
     lib.oracle_ws_features.restype = ctypes.c_int
@@ -169,6 +172,27 @@ def fit(X: np.ndarray, K: int, tol: float = 1e-6, max_iter: int = 1000, algo: in
         raise ValueError("oracle_fit: invalid argument")
     return Fit(T=T, P=P, lam=lam, iters=iters, R=R, found=int(found[0]), status=int(st), ws_choice=choice,
                ws_rho=None if rho is None else rho.reshape(K, 2))
+
+
+def block_fit(X: np.ndarray, K: int, b: int, tol: float = 1e-6, max_iter: int = 1000, iters_lock=None,
+              flavor: str = "O2") -> Fit:
+    """Block power iteration (oracle.c, oracle_block_fit): components b at a time, FP64."""
+    X = np.asfortranarray(np.asarray(X, dtype=np.float64))
+    M, N = X.shape
+    T = np.zeros((M, K), order="F")
+    P = np.zeros((N, K), order="F")
+    R = np.zeros((M, N), order="F")
+    lam = np.zeros(K)
+    iters = np.zeros(K, dtype=np.int32)
+    found = np.zeros(1, dtype=np.int32)
+    lock = None
+    if iters_lock is not None:
+        lock = np.ascontiguousarray(np.asarray(iters_lock, dtype=np.int32))
+    st = _load(flavor).oracle_block_fit(_dptr(X), M, N, K, int(b), float(tol), int(max_iter), _iptr(lock), _dptr(T),
+                                        _dptr(P), _dptr(lam), _iptr(iters), _dptr(R), _iptr(found))
+    if st == 1:
+        raise ValueError("oracle_block_fit: invalid argument")
+    return Fit(T=T, P=P, lam=lam, iters=iters, R=R, found=int(found[0]), status=int(st))
 
 
 # ------------------------------------------------------------ learned warm start

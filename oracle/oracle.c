@@ -573,3 +573,211 @@ int oracle_jacobi_eigh(double *A, int n, double tol, int max_sweeps, double *eva
     free(W);
     return done ? sweep : -2;
 }
+
+/* ------------------------------------------------ block (subspace) iteration */
+
+/* Thin QR of the rows x cols matrix A (column-major) by classical Gram-Schmidt
+ * applied twice per column (CGS2): A <- Q with orthonormal columns, Rf (cols x
+ * cols, column-major, upper triangular, positive diagonal) with A_in = Q Rf.
+ * Returns the index of the first column that is numerically dependent
+ * (norm after projection <= 64 eps of its norm before), or -1. */
+static int qr_cgs2(double *A, int rows, int cols, double *Rf)
+{
+    for (int i = 0; i < cols * cols; i++)
+        Rf[i] = 0.0;
+    double *c = malloc(sizeof(double) * (size_t)(cols > 0 ? cols : 1));
+    if (!c)
+        return 0;
+    for (int j = 0; j < cols; j++) {
+        double *a = A + (size_t)j * rows;
+        const double n0 = nrm2(a, rows);
+        for (int pass = 0; pass < 2 && j > 0; pass++) {
+            gemv_t(A, rows, j, a, c);
+            for (int i = 0; i < j; i++) {
+                const double *q = A + (size_t)i * rows;
+                for (int r = 0; r < rows; r++)
+                    a[r] -= q[r] * c[i];
+                Rf[(size_t)j * cols + i] += c[i];
+            }
+        }
+        const double n1 = nrm2(a, rows);
+        if (!(n1 > 64.0 * DBL_EPSILON * n0) || n1 == 0.0) {
+            free(c);
+            return j;
+        }
+        scal(a, rows, 1.0 / n1);
+        Rf[(size_t)j * cols + j] = n1;
+    }
+    free(c);
+    return -1;
+}
+
+/* C (m x n) = A^T B for A (rows x m), B (rows x n), column-major. */
+static void gemm_tn(const double *A, const double *B, int rows, int m, int n, double *C)
+{
+    for (int j = 0; j < n; j++)
+        gemv_t(A, rows, m, B + (size_t)j * rows, C + (size_t)j * m);
+}
+
+/* Y (rows x n) = A (rows x cols) B (cols x n), column-major. */
+static void gemm_nn(const double *A, const double *B, int rows, int cols, int n, double *Y)
+{
+    for (int j = 0; j < n; j++)
+        gemv_n(A, rows, cols, B + (size_t)j * cols, Y + (size_t)j * rows);
+}
+
+/* X <- X - Q (Q^T X) for Q (rows x k, orthonormal columns) and X (rows x n). */
+static void project_out(const double *Q, int rows, int k, double *X, int n, double *tmp)
+{
+    if (k == 0)
+        return;
+    gemm_tn(Q, X, rows, k, n, tmp);
+    for (int j = 0; j < n; j++)
+        for (int i = 0; i < k; i++) {
+            const double c = tmp[(size_t)j * k + i];
+            const double *q = Q + (size_t)i * rows;
+            double *x = X + (size_t)j * rows;
+            for (int r = 0; r < rows; r++)
+                x[r] -= q[r] * c;
+        }
+}
+
+/* Block power iteration (subspace iteration with Rayleigh-Ritz), the block
+ * form of the GS-PCA loop of Sec. 2.3 (not in the paper): components are
+ * extracted b at a time.  For a block of width b (the last one narrower):
+ *   U <- R^T R(:, k0 .. k0+b-1)  (the paper's start v = R(k), u = R^T v, for b columns)
+ *   U <- U - U_(k0) U_(k0)^T U ; U <- qr(U)
+ *   repeat: Y <- R U ; Y <- Y - V_(k0) V_(k0)^T Y ; V <- qr(Y)
+ *           Z <- R^T V ; Z <- Z - U_(k0) U_(k0)^T Z
+ *           s <- singular values of Z, decreasing (the Ritz values)
+ *           stop when |s_i - s_i'| < tol s_i for every i (s' of the previous iteration,
+ *           0 at first) or after max_iter iterations; otherwise U <- qr(Z)
+ *   Rayleigh-Ritz: B = V^T R U = Z^T U (b x b), B = Yh diag(sigma) Zh^T (decreasing),
+ *   V <- V Yh, U <- U Zh, lambda = sigma;  R <- R - V diag(lambda) U^T (Eq. 3 for b columns).
+ * T = V Lambda, P = U (Eq. 5).  qr is CGS2; the singular values come from the
+ * Jacobi eigensolver below applied to Z^T Z and B^T B.  A start or iterate whose
+ * columns become numerically dependent stops the fit as degenerate (the
+ * components of earlier blocks are kept).  iters_lock (nullable, K entries):
+ * block starting at k0 runs exactly iters_lock[k0] iterations.  Every component
+ * of a block reports the block's iteration count. */
+int oracle_block_fit(const double *X, int M, int N, int K, int b, double tol, int max_iter, const int *iters_lock,
+                     double *T, double *P, double *lambda, int *iters, double *R, int *found)
+{
+    if (!X || !T || !P || !lambda || !iters || !R || !found)
+        return OR_INVALID;
+    if (M < 1 || N < 1 || K < 1 || K > M || K > N || b < 1 || !(tol > 0.0) || max_iter < 1)
+        return OR_INVALID;
+    memcpy(R, X, sizeof(double) * (size_t)M * N);
+    const int B = b < K ? b : K;
+    double *U = malloc(sizeof(double) * (size_t)N * B), *Y = malloc(sizeof(double) * (size_t)M * B);
+    double *Z = malloc(sizeof(double) * (size_t)N * B), *Rf = malloc(sizeof(double) * (size_t)B * B);
+    double *G = malloc(sizeof(double) * (size_t)B * B), *E = malloc(sizeof(double) * (size_t)B * B);
+    double *s = malloc(sizeof(double) * (size_t)B), *sp = malloc(sizeof(double) * (size_t)B);
+    double *tmp = malloc(sizeof(double) * (size_t)K * B), *Bm = malloc(sizeof(double) * (size_t)B * B);
+    double *Zh = malloc(sizeof(double) * (size_t)B * B), *Yh = malloc(sizeof(double) * (size_t)M * B);
+    double *Un = malloc(sizeof(double) * (size_t)N * B);
+    int status = OR_OK, kf = 0, not_converged = 0;
+    if (!U || !Y || !Z || !Rf || !G || !E || !s || !sp || !tmp || !Bm || !Zh || !Yh || !Un) {
+        status = OR_INVALID;
+        goto out;
+    }
+    for (int k0 = 0; k0 < K; k0 += B) {
+        const int bw = (K - k0) < B ? (K - k0) : B;
+        double *Vp = T, *Up = P; /* V_(k0), U_(k0): the first k0 columns (unit columns until the end) */
+        gemm_tn(R, R + (size_t)k0 * M, M, N, bw, U); /* U = R^T R(:, k0 .. k0+bw-1) */
+        project_out(Up, N, k0, U, bw, tmp);
+        if (qr_cgs2(U, N, bw, Rf) >= 0) {
+            status = OR_DEGENERATE;
+            break;
+        }
+        for (int i = 0; i < bw; i++)
+            sp[i] = 0.0;
+        int j = 0;
+        for (;;) {
+            gemm_nn(R, U, M, N, bw, Y);
+            project_out(Vp, M, k0, Y, bw, tmp);
+            if (qr_cgs2(Y, M, bw, Rf) >= 0) {
+                status = OR_DEGENERATE;
+                break;
+            }
+            gemm_tn(R, Y, M, N, bw, Z); /* Z = R^T V */
+            project_out(Up, N, k0, Z, bw, tmp);
+            gemm_tn(Z, Z, N, bw, bw, G);
+            if (oracle_jacobi_eigh(G, bw, 1e-15, 100, s, E) == -1) {
+                status = OR_INVALID;
+                break;
+            }
+            for (int i = 0; i < bw; i++)
+                s[i] = sqrt(s[i] > 0.0 ? s[i] : 0.0);
+            j++;
+            int stop;
+            if (iters_lock) {
+                stop = j >= iters_lock[k0];
+            } else {
+                stop = 1;
+                for (int i = 0; i < bw; i++)
+                    if (!(fabs(sp[i] - s[i]) < tol * s[i]))
+                        stop = 0;
+                if (!stop && j >= max_iter) {
+                    stop = 1;
+                    not_converged = 1;
+                }
+            }
+            if (stop)
+                break;
+            for (int i = 0; i < bw; i++)
+                sp[i] = s[i];
+            memcpy(U, Z, sizeof(double) * (size_t)N * bw);
+            if (qr_cgs2(U, N, bw, Rf) >= 0) {
+                status = OR_DEGENERATE;
+                break;
+            }
+        }
+        if (status != OR_OK)
+            break;
+        /* Rayleigh-Ritz: B = Z^T U, B^T B = Zh diag(sigma^2) Zh^T, Yh = B Zh / sigma */
+        gemm_tn(Z, U, N, bw, bw, Bm);
+        gemm_tn(Bm, Bm, bw, bw, bw, G);
+        if (oracle_jacobi_eigh(G, bw, 1e-15, 100, s, Zh) == -1) {
+            status = OR_INVALID;
+            break;
+        }
+        int deg = 0;
+        for (int i = 0; i < bw; i++) {
+            s[i] = sqrt(s[i] > 0.0 ? s[i] : 0.0);
+            if (!(s[i] > 0.0))
+                deg = 1;
+        }
+        if (deg) {
+            status = OR_DEGENERATE;
+            break;
+        }
+        gemm_nn(Bm, Zh, bw, bw, bw, E); /* E = B Zh (columns sigma_i times Yh) */
+        for (int i = 0; i < bw; i++)
+            scal(E + (size_t)i * bw, bw, 1.0 / s[i]);
+        gemm_nn(Y, E, M, bw, bw, Yh); /* V Yh */
+        gemm_nn(U, Zh, N, bw, bw, Un); /* U Zh */
+        for (int i = 0; i < bw; i++) {
+            memcpy(T + (size_t)(k0 + i) * M, Yh + (size_t)i * M, sizeof(double) * M);
+            memcpy(P + (size_t)(k0 + i) * N, Un + (size_t)i * N, sizeof(double) * N);
+            lambda[k0 + i] = s[i];
+            iters[k0 + i] = j;
+        }
+        for (int i = 0; i < bw; i++)
+            ger(R, M, N, -s[i], T + (size_t)(k0 + i) * M, P + (size_t)(k0 + i) * N);
+        kf = k0 + bw;
+    }
+    if (status == OR_OK && not_converged)
+        status = OR_NOT_CONVERGED;
+out:
+    if (status != OR_INVALID) {
+        for (int k = 0; k < kf; k++)
+            scal(T + (size_t)k * M, M, lambda[k]);
+        if (kf < K)
+            zero_tail(T, P, lambda, iters, M, N, K, kf);
+        *found = kf;
+    }
+    free(U), free(Y), free(Z), free(Rf), free(G), free(E), free(s), free(sp), free(tmp), free(Bm), free(Zh), free(Yh),
+        free(Un);
+    return status;
+}
