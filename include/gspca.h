@@ -226,6 +226,29 @@ gspca_status gspca_fit_f64(gspca_t h, void *stream, const double *X, gspca_layou
                            int K, double tol, int max_iter, gspca_algo algo, double *T, double *P, double *lambda,
                            int *iters, double *R_out, const gspca_opts *opts);
 
+/* Block power iteration: components `block` at a time (1 <= block <= 32), the
+ * block form of the Sec. 2.3 loop; the paper has no counterpart (it extracts one
+ * component at a time).  For a block of width b starting at component k0:
+ *   U = R^T R(:, k0 .. k0+b-1), made orthogonal to P(:, 0:k0) and orthonormal;
+ *   repeat: Y = R U, made orthogonal to the earlier score directions, V = qr(Y);
+ *           Z = R^T V, made orthogonal to P(:, 0:k0); Ritz values s = singular
+ *           values of Z; stop when every |s_i - s_i(previous)| < tol s_i, after
+ *           max_iter iterations or after iters_lock[k0] (opts); else U = qr(Z);
+ *   Rayleigh-Ritz: B = V^T R U = Yh diag(sigma) Zh^T (sigma decreasing),
+ *   V <- V Yh, U <- U Zh, lambda = sigma; R <- R - V diag(lambda) U^T (Eq. 3).
+ * Outputs as gspca_fit (T = V Lambda, or V with opts->svd_form = 1; P = U; every
+ * component of a block reports the block's iteration count).  The products with
+ * R and the projections are FP32 matrix products (cuBLAS); qr is Cholesky QR
+ * applied twice with FP64 Gram matrices.  A GSPCA_F32 handle; X FP32 device
+ * memory; opts: center, iters_lock, svd_form apply (warm, gs_passes = 2 and
+ * coef_trace give GSPCA_ERR_NOT_SUPPORTED).  A block whose start or iterate has
+ * numerically dependent columns ends the fit with GSPCA_ERR_DEGENERATE (earlier
+ * blocks kept).  The first call on a handle allocates the block workspace and a
+ * cuBLAS handle (owned by the handle).  Synchronises `stream` once per iteration. */
+gspca_status gspca_fit_block(gspca_t h, void *stream, const float *X, gspca_layout layout, long ldx, int M, int N,
+                             int K, int block, double tol, int max_iter, float *T, float *P, double *lambda,
+                             int *iters, float *R_out, const gspca_opts *opts);
+
 /* One independent problem of a batch (device pointers, same conventions as
  * gspca_fit, column-major X with leading dimension ldx). */
 typedef struct {

@@ -32,7 +32,8 @@ GSPCA_ERR_NOT_SUPPORTED = 7
 
 EXPORTS = ["gspca_create", "gspca_fit", "gspca_fit_host", "gspca_fit_batched", "gspca_fit_batched_async",
            "gspca_get_info", "gspca_destroy", "gspca_status_string", "gspca_last_cuda_error",
-           "gspca_fit_noalloc", "gspca_ws_features", "gspca_ws_forward", "gspca_ws_train_step", "gspca_fit_f64"]
+           "gspca_fit_noalloc", "gspca_ws_features", "gspca_ws_forward", "gspca_ws_train_step", "gspca_fit_f64",
+           "gspca_fit_block"]
 
 WS_SKETCH, WS_FEATURES, WS_PARAMS = 16, 17, 5377
 
@@ -99,6 +100,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.gspca_fit_batched.argtypes = [vp, vp, ctypes.POINTER(Problem), i, d, i, i, ctypes.POINTER(Opts)]
     lib.gspca_fit_batched_async.argtypes = [vp, vp, ctypes.POINTER(Problem), i, d, i, i, ctypes.POINTER(Opts), vp]
     lib.gspca_fit_f64.argtypes = fit_args
+    lib.gspca_fit_block.argtypes = [vp, vp, vp, i, l, i, i, i, i, d, i, vp, vp, vp, vp, vp, ctypes.POINTER(Opts)]
+    lib.gspca_fit_block.restype = i
     lib.gspca_fit_noalloc.argtypes = fit_args[1:]
     lib.gspca_fit_noalloc.restype = i
     lib.gspca_ws_features.argtypes = [vp, vp, l, i, i, vp, vp, i, vp, vp]
@@ -299,6 +302,40 @@ def gspca_fit_f64(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, al
     return FitResult(T, P, lam, iters, R, st, gspca_get_info(h))
 
 
+def gspca_fit_block(h: int, X, K: int, block: int = 16, tol: float = 1e-6, max_iter: int = 1000, center: int = 0,
+                    iters_lock=None, want_R: bool = False, stream=None, check: bool = True,
+                    svd_form: int = 0) -> FitResult:
+    """Block power iteration (components `block` at a time) on a float32 handle; X a 2-D float32
+    CUDA tensor.  iters_lock: K counts, entry k0 fixes the iterations of the block starting at k0."""
+    import torch
+
+    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
+        raise TypeError("X must be a 2-D float32 CUDA tensor")
+    layout, ldx = _layout_of(X)
+    if layout is None:
+        X = X.contiguous()
+        layout, ldx = GSPCA_ROW_MAJOR, X.shape[1]
+    M, N = X.shape
+    dev = X.device
+    T = torch.empty((K, M), device=dev, dtype=torch.float32).t()
+    P = torch.empty((K, N), device=dev, dtype=torch.float32).t()
+    lam = torch.empty(K, device=dev, dtype=torch.float64)
+    iters = torch.empty(K, device=dev, dtype=torch.int32)
+    R = torch.empty((N, M), device=dev, dtype=torch.float32).t() if want_R else None
+    if stream is None:
+        stream = torch.cuda.current_stream(dev).cuda_stream
+    o, keep = _opts(center, iters_lock, svd_form=svd_form)
+    st = load().gspca_fit_block(ctypes.c_void_p(h), ctypes.c_void_p(stream), ctypes.c_void_p(X.data_ptr()), layout,
+                                int(ldx), M, N, int(K), int(block), float(tol), int(max_iter),
+                                ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(P.data_ptr()),
+                                ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(iters.data_ptr()),
+                                ctypes.c_void_p(R.data_ptr()) if R is not None else None, ctypes.byref(o))
+    del keep
+    if check and st not in (GSPCA_OK, GSPCA_WARN_NOT_CONVERGED, GSPCA_ERR_DEGENERATE):
+        raise GspcaError(st, "gspca_fit_block")
+    return FitResult(T, P, lam, iters, R, st, gspca_get_info(h))
+
+
 def gspca_fit_host(h: int, X, K: int, tol: float = 1e-6, max_iter: int = 1000, algo="gs",
                    center: int = 0, iters_lock=None, want_R: bool = False, stream=None,
                    out=None, check: bool = True, gs_passes: int = 0, svd_form: int = 0) -> FitResult:
@@ -359,6 +396,9 @@ class Handle:
 
     def fit64(self, X, K, **kw) -> FitResult:
         return gspca_fit_f64(self.h, X, K, **kw)
+
+    def fit_block(self, X, K, **kw) -> FitResult:
+        return gspca_fit_block(self.h, X, K, **kw)
 
     def info(self) -> dict:
         return gspca_get_info(self.h)

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libgspca.so")
-SOURCES = ["gspca_api.cu", "noalloc_api.cu", "batch_api.cu", "warmstart_api.cu", "fit64_api.cu",
+SOURCES = ["gspca_api.cu", "noalloc_api.cu", "batch_api.cu", "warmstart_api.cu", "fit64_api.cu", "block_api.cu",
            "fit_f32_a.cu", "fit_f32_b.cu", "fit_f32_c.cu", "fit_bf16_a.cu", "fit_bf16_b.cu", "fit_bf16_c.cu",
            "fit_f32_w.cu", "fit_bf16_w.cu", "fit_f32_g.cu", "fit_bf16_g.cu",
            "fit_f32_k.cu", "fit_bf16_k.cu"]
@@ -56,7 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if p.wait() != 0:
             raise RuntimeError("nvcc failed: " + " ".join(cmd))
     tmp = LIB + ".tmp"
-    cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcublas"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

@@ -315,6 +315,7 @@ gspca_status gspca_destroy(gspca_t h) {
     if (h->stage && !cuda_ok(cudaFree(h->stage))) st = GSPCA_ERR_CUDA;
     if (h->ws_base && !cuda_ok(cudaFree(h->ws_base))) st = GSPCA_ERR_CUDA;
     if (h->ws64_base && !cuda_ok(cudaFree(h->ws64_base))) st = GSPCA_ERR_CUDA;
+    if (block_release(h) != GSPCA_OK) st = GSPCA_ERR_CUDA;
     if (h->ws_train && !cuda_ok(cudaFree(h->ws_train))) st = GSPCA_ERR_CUDA;
     if (h->h_info && !cuda_ok(cudaFreeHost(h->h_info))) st = GSPCA_ERR_CUDA;
     if (h->ev0) cudaEventDestroy(h->ev0);

@@ -50,6 +50,8 @@ struct gspca_handle;
 namespace gspca {
 // Allocate the FP64 workspace of a GSPCA_F64 handle (fit64_api.cu).
 gspca_status create_ws64(gspca_handle* h);
+// Release what gspca_fit_block allocated (block_api.cu).
+gspca_status block_release(gspca_handle* h);
 }  // namespace gspca
 
 #define GS_CUDA(call)                                     \
@@ -78,4 +80,7 @@ struct gspca_handle {
     size_t ws_train_bytes = 0;
     void* ws64_base = nullptr;      // GSPCA_F64 handles: the FP64 workspace (instead of ws)
     gspca::Workspace64 ws64{};
+    void* blk_base = nullptr;       // gspca_fit_block: block workspace (allocated on first use)
+    void* cublas = nullptr;         // its cuBLAS handle
+    int* h_blk = nullptr;           // pinned flag word
 };
