@@ -560,15 +560,19 @@ __device__ __forceinline__ bool pass_dot2(const FitArgs& f, SmemFit& sm, Ring& r
     ring_prefetch<E>(f, rg, p0, p1, 1);
     const unsigned base = rg.used;
     const int nrounds = p1 - p0;
+    // stage and mbarrier phase of the group's first round; each later round of the group is
+    // two sequences on (S is even: the group keeps to the stages of one parity)
+    int sidx = (int)((base + (unsigned)grp) % (unsigned)rg.S);
+    unsigned ph = ((base + (unsigned)grp) / (unsigned)rg.S) & 1u;
     for (int round = grp; round < nrounds; round += 2) {
         const int p = p0 + round;
-        const unsigned q = base + (unsigned)round;
+        uint64_t* mb = reinterpret_cast<uint64_t*>(&rg.mbar[sidx]);
         if (f.stall_word && round == grp && !stall_wait(f)) ok = 0;
-        if (!mbar_wait(rg.bar(q), (q / rg.S) & 1u, f.timeout_ns)) {
+        if (!mbar_wait(mb, ph, f.timeout_ns)) {
             ok = 0;  // reported; the stage is still awaited before it is read or refilled
-            mbar_wait(rg.bar(q), (q / rg.S) & 1u, kSettleNs);
+            mbar_wait(mb, ph, kSettleNs);
         }
-        const unsigned char* st = rg.stage(q);
+        unsigned char* st = rg.base + (size_t)sidx * rg.stage_bytes;
         float4 d[C2];
 #pragma unroll
         for (int i = 0; i < C2; ++i) {
@@ -589,8 +593,8 @@ __device__ __forceinline__ bool pass_dot2(const FitArgs& f, SmemFit& sm, Ring& r
         named_barrier(1 + grp, 256);
         // this group has read the stage: refill it with round + S (same group)
         if (lt == 0 && round + rg.S < nrounds)
-            tma_load_1d(rg.stage(q + rg.S), static_cast<const unsigned char*>(f.R) + (size_t)(p + rg.S) * ldp * CB,
-                        (uint32_t)ldp * (uint32_t)CB, rg.bar(q + rg.S));
+            tma_load_1d(st, static_cast<const unsigned char*>(f.R) + (size_t)(p + rg.S) * ldp * CB,
+                        (uint32_t)ldp * (uint32_t)CB, mb);
         float rs = 0.f;
         if (lane < 4)
 #pragma unroll
@@ -608,6 +612,11 @@ __device__ __forceinline__ bool pass_dot2(const FitArgs& f, SmemFit& sm, Ring& r
             sacc2[i] = fmaf(d[i].y, rowv[1], sacc2[i]);
             sacc2[i] = fmaf(d[i].z, rowv[2], sacc2[i]);
             sacc2[i] = fmaf(d[i].w, rowv[3], sacc2[i]);
+        }
+        sidx += 2;
+        if (sidx >= rg.S) {
+            sidx -= rg.S;
+            ph ^= 1u;
         }
     }
     rg.used = base + (unsigned)nrounds;
@@ -1205,37 +1214,25 @@ __device__ __forceinline__ void matrix_times_vector(const float* A, int lda, int
 // For every row r in [r0, r1): fn(r, A_r . x, B_r . y, pre(r)) with kk <= 64
 // columns and x, y in shared memory; each product in the order of the general
 // path of matrix_times_vector.
+// A warp takes rows r0 + warp, r0 + warp + 16, ... one at a time: the rows are a
+// CTA's slice of the N columns (a few dozen), so a wider unrolled block would mostly
+// carry masked rows through its shuffles.
 template <class Pre, class Fn>
 __device__ __forceinline__ void matrix_times_two(const float* A, const float* B, int lda, int r0, int r1, int kk,
                                                  const float* x, const float* y, Pre pre, Fn fn) {
-    constexpr int MAXR = 8;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const bool c0 = lane < kk, c1 = lane + 32 < kk;
     const float x0 = c0 ? x[lane] : 0.f, x1 = c1 ? x[lane + 32] : 0.f;
     const float y0 = c0 ? y[lane] : 0.f, y1 = c1 ? y[lane + 32] : 0.f;
-    for (int rb = r0 + warp; rb < r1; rb += nw * MAXR) {
-        float accA[MAXR], accB[MAXR], pv[MAXR];
-#pragma unroll
-        for (int i = 0; i < MAXR; ++i) {
-            const int r = rb + nw * i;
-            const bool ok = r < r1;
-            pv[i] = ok ? pre(r) : 0.f;
-            const float* ar = A + (size_t)r * lda;
-            const float* br = B + (size_t)r * lda;
-            const float a0 = (ok && c0) ? ar[lane] : 0.f, a1 = (ok && c1) ? ar[lane + 32] : 0.f;
-            const float b0 = (ok && c0) ? br[lane] : 0.f, b1 = (ok && c1) ? br[lane + 32] : 0.f;
-            accA[i] = fmaf(a1, x1, fmaf(a0, x0, 0.f));
-            accB[i] = fmaf(b1, y1, fmaf(b0, y0, 0.f));
-        }
-        const float sA = warp_multi_reduce<MAXR>(accA, lane);  // lane l: row index l >> 2
-        const float sB = warp_multi_reduce<MAXR>(accB, lane);
-        const int i = lane >> 2;
-        float p = pv[0];
-#pragma unroll
-        for (int t = 1; t < MAXR; ++t)
-            if (t == i) p = pv[t];
-        const int r = rb + nw * i;
-        if ((lane & 3) == 0 && r < r1) fn(r, sA, sB, p);
+    for (int r = r0 + warp; r < r1; r += nw) {
+        const float pv = pre(r);
+        const float* ar = A + (size_t)r * lda;
+        const float* br = B + (size_t)r * lda;
+        const float a0 = c0 ? ar[lane] : 0.f, a1 = c1 ? ar[lane + 32] : 0.f;
+        const float b0 = c0 ? br[lane] : 0.f, b1 = c1 ? br[lane + 32] : 0.f;
+        const float sA = warp_sum(fmaf(a1, x1, fmaf(a0, x0, 0.f)));
+        const float sB = warp_sum(fmaf(b1, y1, fmaf(b0, y0, 0.f)));
+        if (lane == 0) fn(r, sA, sB, pv);
     }
 }
 
@@ -2407,27 +2404,35 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                 PHASE_MARK(6);
                 if (try2) {
                     // a' = U^T (s' - W b') = c' - Z b' and ||v' - V b'||^2 = ||v'||^2 - 2 b'.b' +
-                    // b'^T (V^T V) b' from reduced values only (one warp, fixed order); taken when
-                    // the subtraction loses little (b'.b' <= ||v'||^2 / 4).
+                    // b'^T (V^T V) b' from reduced values only (fixed order); taken when the
+                    // subtraction loses little (b'.b' <= ||v'||^2 / 4).  Warp w sums the rows j
+                    // of its chunk of V^T V and Z against b' for every column i (k <= 64), then
+                    // warp 0 adds the 16 warp partials in warp order.
+                    {
+                        const int jc = (k + kMaxWarps - 1) / kMaxWarps;
+                        const int ja = warp * jc, jb = min(k, ja + jc);
+                        for (int i = lane; i < k; i += 32) {
+                            float t = 0.f, z = 0.f;
+                            for (int jj = ja; jj < jb; ++jj) {
+                                const float b = kb[jj];
+                                t = fmaf(GVs[(size_t)jj * f.ldk + i], b, t);
+                                z = fmaf(Zs[(size_t)jj * f.ldk + i], b, z);
+                            }
+                            sm.tmpf[warp][i] = t;
+                            sm.tmpf[warp][64 + i] = z;
+                        }
+                    }
+                    __syncthreads();
                     if (warp == 0) {
                         const float* kc = kb + k;
                         ff bb = ff_zero(), bg = ff_zero();
                         for (int i = lane; i < k; i += 32) {
-                            // even and odd j in separate chains (twice the independent FMAs)
-                            float t0 = 0.f, t1 = 0.f, z0 = 0.f, z1 = 0.f;
-                            int jj = 0;
-                            for (; jj + 1 < k; jj += 2) {
-                                const float b0 = kb[jj], b1 = kb[jj + 1];
-                                t0 = fmaf(GVs[(size_t)jj * f.ldk + i], b0, t0);
-                                z0 = fmaf(Zs[(size_t)jj * f.ldk + i], b0, z0);
-                                t1 = fmaf(GVs[(size_t)(jj + 1) * f.ldk + i], b1, t1);
-                                z1 = fmaf(Zs[(size_t)(jj + 1) * f.ldk + i], b1, z1);
+                            float t = 0.f, z = 0.f;
+#pragma unroll
+                            for (int w = 0; w < kMaxWarps; ++w) {
+                                t += sm.tmpf[w][i];
+                                z += sm.tmpf[w][64 + i];
                             }
-                            if (jj < k) {
-                                t0 = fmaf(GVs[(size_t)jj * f.ldk + i], kb[jj], t0);
-                                z0 = fmaf(Zs[(size_t)jj * f.ldk + i], kb[jj], z0);
-                            }
-                            const float t = t0 + t1, z = z0 + z1;
                             ka[i] = kc[i] - z;
                             bb = ff_add(bb, ff_sqr(kb[i]));
                             bg = ff_add(bg, ff_mul_ff(kb[i], t));
