@@ -514,6 +514,33 @@ def bench_batched(gp, dev, args):
     return out
 
 
+def run_once(gp, args):
+    """One fit of --workload (or one launch of the 256-problem batch) on cuda:0 for an ncu
+    capture: the library's kernels run exactly as in the timed legs, nothing is timed."""
+    import torch
+
+    if args.once_batched:
+        shapes = synth.batch_shapes()
+        cols = [torch.from_numpy(synth.batch_problem(i, M, N).X.astype(np.float32)).cuda().t().contiguous().t()
+                for i, (M, N) in enumerate(shapes)]
+        with gp.Handle(max(m for m, _ in shapes), max(n for _, n in shapes), 16) as h:
+            _, st = gp.gspca_fit_batched(h.h, gp.Batch([{"X": X, "K": 16} for X in cols]), cluster_ctas=4,
+                                         batch_pass=1)
+            torch.cuda.synchronize()
+            print("batched", len(cols), "problems:", gp.status_string(st), f"{h.info()['kernel_ms']:.2f} ms")
+        return 0
+    w = synth.WORKLOADS[args.workload]
+    K = args.K or w.K
+    max_iter = args.max_iter or w.max_iter
+    Xd = torch.from_numpy(w.make().astype(np.float32)).cuda()
+    with gp.Handle(w.M, w.N, K, dtype=args.storage) as h:
+        r = h.fit(Xd, K, tol=w.tol, max_iter=max_iter, algo=args.algo, check=False)
+        torch.cuda.synchronize()
+        print(f"{w.name} K={K} {args.algo} {args.storage}: {gp.status_string(r.status)}, "
+              f"{r.info['kernel_ms']:.2f} ms, {r.info['total_iters']} iterations")
+    return 0 if r.status in (gp.GSPCA_OK, gp.GSPCA_WARN_NOT_CONVERGED) else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -535,6 +562,13 @@ def main():
                     help="skip the secondary HBM-streaming measurement (15000 x 7500 uniform, R = 450 MB)")
     ap.add_argument("--no-other-algo", action="store_true",
                     help="skip the secondary measurement of the other algorithm on the same workload")
+    ap.add_argument("--once", action="store_true",
+                    help="profiling aid: one fit of --workload (no timing, no JSON line), then exit")
+    ap.add_argument("--once-batched", action="store_true",
+                    help="profiling aid: one launch of the 256-problem FP32 batch (teams of 4 CTAs), then exit")
+    ap.add_argument("--K", type=int, default=0, help="with --once: components (default: the workload's)")
+    ap.add_argument("--max-iter", type=int, default=0,
+                    help="with --once: iteration cap per component (default: the workload's)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -546,6 +580,8 @@ def main():
     import paper_0811_1081_gb300 as gp
 
     gp.load()
+    if args.once or args.once_batched:
+        return run_once(gp, args)
     rank, world, local, dist = dist_setup(args.gpus)
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
