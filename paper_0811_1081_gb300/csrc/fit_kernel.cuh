@@ -25,9 +25,10 @@
 // Barriers per iteration: NIPALS and GS component 0 need two (after the
 // pass; after the new loading); GS components k > 0 need three in the form of
 // Sec. 2.3 (one more after u_pre' = s' - W b' and its coefficients
-// a' = U^T u_pre').  With FP32 storage, up to 64 components and 4096 columns
-// per CTA the middle one goes: Q = R_k U and Z = U^T W are kept up to date per
-// component like W, so a' = Q^T v' - Z b' (Q^T v' reduced with b' after the
+// a' = U^T u_pre').  Up to 64 components and 4096 columns per CTA the middle
+// one goes: Q = R_k U and Z = U^T W are kept up to date per component like W
+// (with bfloat16 storage Q's rows are recomputed from the stored residual), so
+// a' = Q^T v' - Z b' (Q^T v' reduced with b' after the
 // pass) and ||v' - V b'||^2 = ||v'||^2 - 2 b'.b' + b'^T V^T V b' come from
 // reduced values, where that is numerically safe (see the guards at the step).
 // The k-vectors are reduced by every CTA from the CTA partials when G*k is
@@ -100,8 +101,8 @@ struct FitArgs {
     int res_rows;             // > 0: this CTA's rows of V (res_rows) and its slices of U and W
                               // (max_slice each) live in shared memory at byte res_off
     int res_off;
-    int gs2;                  // 1 (single-problem GS-PCA, FP32 storage, resident, K <= 64, up to
-                              // 4096 columns per CTA): the
+    int gs2;                  // 1 (single-problem GS-PCA, resident, K <= 64, up to 4096 columns
+                              // per CTA; bfloat16 storage recomputes Q's rows per component): the
                               // resident block also holds this CTA's rows of Q = R_k U_(k) and the
                               // matrices Z = U^T W and V^T V (ldk x ldk), kept up to date per component, and an
                               // iteration may form a' and ||v' - V b'||^2 from them (two grid-wide
@@ -1931,10 +1932,10 @@ constexpr bool kStartColPass = false;
 template <>
 constexpr bool kStartColPass<TeamGrid> = true;
 
-// The two-reduction GS step (FitArgs::gs2) exists in the single-problem kernel
-// for FP32 storage, up to 4096 columns per CTA, without the learned warm start.
+// The two-reduction GS step (FitArgs::gs2) exists in the single-problem kernel,
+// up to 4096 columns per CTA, without the learned warm start.
 template <int CPT, class E, bool WARM, class Team>
-constexpr bool kGs2Step = kStartColPass<Team> && !WARM && CPT <= 8 && Cell<E>::kBytes == 16;
+constexpr bool kGs2Step = kStartColPass<Team> && !WARM && CPT <= 8;
 
 // Fit one problem (f) with a team of CTAs.  The caller provides the
 // degenerate threshold and this CTA's shared memory; the ring must be set up
@@ -1947,6 +1948,79 @@ constexpr bool kGs2Step = kStartColPass<Team> && !WARM && CPT <= 8 && Cell<E>::k
 // A compile-time variant, so the one-pass kernels carry none of its code.
 // WIDE: the factor products take their wide forms past 128 components (the
 // kernel variant chosen for K > 128).
+// bfloat16 storage, two-reduction GS step: this CTA's rows of Q = R_k U_(k)
+// recomputed from the stored residual after each deflation (the rank-1 update
+// the FP32 path uses does not see the bfloat16 rounding of the deflation, and
+// c' = Q^T v' multiplies that error by the whole v').  Thread t takes the
+// panel p0 + t / np2 and the columns 2 (t % np2), +1 (np2 = ceil(k / 2), k <= 64)
+// and sums n = 0 .. N-1 in order in FP32; U reaches shared memory (sm.tmpf) in
+// chunks of 32 rows, the next chunk's values held in registers meanwhile.
+// Measured on the 10000 x 2000, K = 50 fit: about 5 ms per fit in all, against
+// the 10 ms the third grid reduction of every iteration costs.
+template <class E>
+__device__ __forceinline__ void q_rows_from_residual(const FitArgs& f, SmemFit& sm, float* Ql, int p0, int p1,
+                                                     int k) {
+    constexpr int NC = 32;
+    const int tid = threadIdx.x, T = blockDim.x, N = f.N;
+    const int np2 = (k + 1) >> 1;
+    const int units = (p1 - p0) * np2;
+    float* us = &sm.tmpf[0][0];  // NC x 64 floats
+    constexpr int PER = NC * 64 / kBlock;  // staged values per thread and chunk
+    const int nchunks = (N + NC - 1) / NC;
+    for (int u0 = 0; u0 < units; u0 += T) {
+        const int unit = u0 + tid;
+        const bool live = unit < units;
+        const int p = p0 + (live ? unit / np2 : 0);
+        const int i0 = live ? 2 * (unit % np2) : 0;
+        float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
+        float nx[PER];
+        auto fetch = [&](int c) {
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                const int e = tid + j * kBlock, n = c * NC + (e >> 6), i = e & 63;
+                nx[j] = (c < nchunks && n < N && i < k) ? ldcg(f.U + (size_t)n * f.ldu + i) : 0.f;
+            }
+        };
+        fetch(0);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < PER; ++j) us[tid + j * kBlock] = nx[j];
+        fetch(1);
+        __syncthreads();
+        for (int c = 0; c < nchunks; ++c) {
+            const int nn = min(NC, N - c * NC);
+            if (live) {
+                const size_t cell0 = (size_t)p * f.ldp + (size_t)c * NC;
+#pragma unroll 8
+                for (int n = 0; n < nn; ++n) {
+                    const float4 x = Cell<E>::ldg_plain(f.R, cell0 + n);
+                    const float2 uu = *reinterpret_cast<const float2*>(us + n * 64 + i0);
+                    a0[0] = fmaf(x.x, uu.x, a0[0]);
+                    a1[0] = fmaf(x.x, uu.y, a1[0]);
+                    a0[1] = fmaf(x.y, uu.x, a0[1]);
+                    a1[1] = fmaf(x.y, uu.y, a1[1]);
+                    a0[2] = fmaf(x.z, uu.x, a0[2]);
+                    a1[2] = fmaf(x.z, uu.y, a1[2]);
+                    a0[3] = fmaf(x.w, uu.x, a0[3]);
+                    a1[3] = fmaf(x.w, uu.y, a1[3]);
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < PER; ++j) us[tid + j * kBlock] = nx[j];
+            fetch(c + 2);
+            __syncthreads();
+        }
+        if (live)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float* row = Ql + (size_t)(4 * p + q) * f.ldv;
+                row[i0] = a0[q];
+                if (i0 + 1 < k) row[i0 + 1] = a1[q];
+            }
+    }
+}
+
 template <int CPT, class E, bool WARM, class Team, bool CG2 = false, bool WIDE = false>
 __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, unsigned char* dyn_smem, Ring& rg,
                               float threshf, unsigned& epoch) {
@@ -2226,11 +2300,15 @@ __device__ FitOutcome fit_one(const FitArgs& f, const Team& tm, SmemFit& sm, uns
                         *z = fmaf(-lpf * s2, kb[km], vinv_prev * s1);
                     if (i == km || j == km) GVs[(size_t)j * f.ldk + i] = kb[i == km ? j : i];
                 }
-                for (int e = tid; e < (r1 - r0) * k; e += T) {
-                    const int r = r0 + e / k, i = e % k;
-                    const float vk = lpf * Vl[(size_t)r * f.ldv + km];
-                    float* q = Ql + (size_t)r * f.ldv + i;
-                    *q = (i < km) ? fmaf(-vk, h[i], *q) : fmaf(-vk, s2, ldcg(f.vraw + r) * inv_nu);
+                if constexpr (Cell<E>::kBytes == 8) {
+                    q_rows_from_residual<E>(f, sm, Ql, p0, p1, k);
+                } else {
+                    for (int e = tid; e < (r1 - r0) * k; e += T) {
+                        const int r = r0 + e / k, i = e % k;
+                        const float vk = lpf * Vl[(size_t)r * f.ldv + km];
+                        float* q = Ql + (size_t)r * f.ldv + i;
+                        *q = (i < km) ? fmaf(-vk, h[i], *q) : fmaf(-vk, s2, ldcg(f.vraw + r) * inv_nu);
+                    }
                 }
                 __syncthreads();
             } else if (small_k) {

@@ -161,11 +161,11 @@ inline cudaError_t plan_fit(int device, int num_sms, int Gcap, int M, int N, int
         p->res_rows = 4 * np_cta;
         p->res = res;
         // the two-reduction GS step adds this CTA's rows of Q and the two ldk x ldk
-        // matrices; FP32 storage only (Q tracks R U through the deflations without their
-        // rounding, which bfloat16 storage makes far larger than the step's own), up to
-        // 4096 columns (wider rows are dominated by the pass over R)
+        // matrices (with bfloat16 storage the kernel recomputes Q's rows from the stored
+        // residual after each deflation instead of following it by the rank-1 algebra),
+        // up to 4096 columns (wider rows are dominated by the pass over R)
         const size_t extra = sizeof(float) * ((size_t)4 * np_cta * ldf + 2 * (size_t)p->ldk * p->ldk);
-        if (!p->warm && cb == 16 && p->cpt <= 8 && (!opts || opts->gs_step == 0) && p->gs_passes == 1 &&
+        if (!p->warm && p->cpt <= 8 && (!opts || opts->gs_step == 0) && p->gs_passes == 1 &&
             K <= kGs2MaxK &&
             K <= kRedundantMax &&
             res + extra <= kResGs2MaxBytes) {

@@ -278,19 +278,24 @@ def test_resident_factors_do_not_change_results(gp, shape):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
 @pytest.mark.parametrize("shape", [(1003, 517, 6), (10000, 2000, 12), (700, 2000, 40), (64, 4097, 3), (5000, 300, 64)])
-def test_two_reduction_gs_step_matches_three(gp, shape):
+def test_two_reduction_gs_step_matches_three(gp, shape, storage):
     """The Gram-Schmidt step from maintained Q = R U, Z = U^T W and V^T V (two grid-wide
     reductions per iteration) against the three-reduction step of Sec. 2.3: the same fit to
     FP32 rounding (the second run replays the first's iteration counts), and GS-PCA's
     orthogonality kept.  The planted spectrum decays by 0.85 per component, so the larger K
-    also crosses the 64x range beyond which the step falls back to three reductions."""
+    also crosses the 64x range beyond which the step falls back to three reductions.  With
+    bfloat16 storage (Q's rows recomputed from the stored residual per component) a different
+    rounding of v' or u' can round a deflated entry to the neighbouring bfloat16 value, so the
+    bars are the bfloat16 parity bars (1e-4 relative in lambda, 1e-3 rad)."""
     import torch
 
     M, N, K = shape
     X32 = synth.planted(M, N, 5.0, 0.85, 0.01, (43, M, N)).X.astype(np.float32)
     Xd = torch.from_numpy(X32).cuda()
-    with gp.Handle(M, N, K) as h:
+    sig, ang = (1e-5, 1e-4) if storage == "f32" else (1e-4, 1e-3)
+    with gp.Handle(M, N, K, dtype=storage) as h:
         a = h.fit(Xd, K, tol=1e-6, max_iter=1000, algo="gs", gs_step=1)
         lock = [int(v) for v in a.iters.cpu().numpy()]
         b = h.fit(Xd, K, tol=1e-6, max_iter=1000, algo="gs", gs_step=0, iters_lock=lock)
@@ -298,9 +303,23 @@ def test_two_reduction_gs_step_matches_three(gp, shape):
         la, lb = a.lam.cpu().numpy(), b.lam.cpu().numpy()
         Pa, Pb = a.P.cpu().numpy().astype(np.float64), b.P.cpu().numpy().astype(np.float64)
         Ta, Tb = a.T.cpu().numpy().astype(np.float64), b.T.cpu().numpy().astype(np.float64)
-    assert a.status == 0 and b.status == 0
-    assert np.all(np.abs(la - lb) <= 1e-5 * la)
-    for k in range(K):
-        assert angle(Pa[:, k], Pb[:, k]) <= 1e-4
-        assert angle(Ta[:, k], Tb[:, k]) <= 1e-4
+    if storage == "f32":
+        assert a.status == 0 and b.status == 0
+        assert np.all(np.abs(la - lb) <= sig * la)
+        for k in range(K):
+            assert angle(Pa[:, k], Pb[:, k]) <= ang
+            assert angle(Ta[:, k], Tb[:, k]) <= ang
+    else:
+        # the second run stops on the replayed counts (status 0) where the first hit max_iter;
+        # near the noise floor of the planted spectrum (the largest singular value of the 0.01
+        # noise is about 0.01 (sqrt(M) + sqrt(N))) the singular values form a bulk whose members
+        # bfloat16 rounding mixes, so the components above twice that are compared
+        assert a.status in (0, 4) and b.status in (0, 4)
+        kk = int(np.sum(la >= 2 * 0.01 * (math.sqrt(M) + math.sqrt(N))))
+        assert kk >= min(3, K)
+        assert np.all(np.abs(la[:kk] - lb[:kk]) <= sig * la[:kk])
+        for k in range(kk):
+            assert angle(Pa[:, k], Pb[:, k]) <= ang
+            assert angle(Ta[:, k], Tb[:, k]) <= ang
+    assert np.abs(Pb.T @ Pb - np.eye(K)).max() <= ORTHO
     assert np.abs(Pb.T @ Pb - np.eye(K)).max() <= ORTHO
