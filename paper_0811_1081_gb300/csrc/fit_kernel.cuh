@@ -1951,49 +1951,58 @@ constexpr bool kGs2Step = kStartColPass<Team> && !WARM && CPT <= 8;
 // bfloat16 storage, two-reduction GS step: this CTA's rows of Q = R_k U_(k)
 // recomputed from the stored residual after each deflation (the rank-1 update
 // the FP32 path uses does not see the bfloat16 rounding of the deflation, and
-// c' = Q^T v' multiplies that error by the whole v').  Thread t takes the
-// panel p0 + t / np2 and the columns 2 (t % np2), +1 (np2 = ceil(k / 2), k <= 64)
-// and sums n = 0 .. N-1 in order in FP32; U reaches shared memory (sm.tmpf) in
-// chunks of 32 rows, the next chunk's values held in registers meanwhile.
-// Measured on the 10000 x 2000, K = 50 fit: about 5 ms per fit in all, against
-// the 10 ms the third grid reduction of every iteration costs.
+// c' = Q^T v' multiplies that error by the whole v').  Panels go in rounds of up
+// to 32; in a round thread t takes panel t / np2 and the columns 2 (t % np2), +1
+// (np2 = ceil(k / 2), k <= 64) and sums n = 0 .. N-1 in order in FP32.  U (16
+// rows x 64) and the round's cells of R (16 columns per panel) reach shared
+// memory (sm.tmpf) chunk by chunk, the next chunk held in registers meanwhile,
+// so no thread waits on L2 inside a chunk.
 template <class E>
 __device__ __forceinline__ void q_rows_from_residual(const FitArgs& f, SmemFit& sm, float* Ql, int p0, int p1,
                                                      int k) {
-    constexpr int NC = 32;
-    const int tid = threadIdx.x, T = blockDim.x, N = f.N;
+    constexpr int NC = 16, PRMAX = 32;
+    constexpr int PER = NC * 64 / kBlock;  // staged U values per thread and chunk
+    const int tid = threadIdx.x, N = f.N;
     const int np2 = (k + 1) >> 1;
-    const int units = (p1 - p0) * np2;
-    float* us = &sm.tmpf[0][0];  // NC x 64 floats
-    constexpr int PER = NC * 64 / kBlock;  // staged values per thread and chunk
+    const int pr = min(PRMAX, kBlock / np2);
+    float* us = &sm.tmpf[0][0];                                       // NC x 64 floats
+    uint2* rs = reinterpret_cast<uint2*>(&sm.tmpf[0][0] + NC * 64);  // pr x NC cells
+    const uint2* R = static_cast<const uint2*>(f.R);
     const int nchunks = (N + NC - 1) / NC;
-    for (int u0 = 0; u0 < units; u0 += T) {
-        const int unit = u0 + tid;
-        const bool live = unit < units;
-        const int p = p0 + (live ? unit / np2 : 0);
-        const int i0 = live ? 2 * (unit % np2) : 0;
+    for (int pa = p0; pa < p1; pa += pr) {
+        const int pn = min(pr, p1 - pa);
+        const bool live = tid < pn * np2;
+        const int pl = live ? tid / np2 : 0;
+        const int i0 = live ? 2 * (tid % np2) : 0;
         float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
         float nx[PER];
+        uint2 nr;
         auto fetch = [&](int c) {
 #pragma unroll
             for (int j = 0; j < PER; ++j) {
                 const int e = tid + j * kBlock, n = c * NC + (e >> 6), i = e & 63;
                 nx[j] = (c < nchunks && n < N && i < k) ? ldcg(f.U + (size_t)n * f.ldu + i) : 0.f;
             }
+            const int pp = tid / NC, n = c * NC + tid % NC;
+            nr = (c < nchunks && pp < pn && n < N) ? ldcg(R + (size_t)(pa + pp) * f.ldp + n) : make_uint2(0u, 0u);
+        };
+        auto put = [&]() {
+#pragma unroll
+            for (int j = 0; j < PER; ++j) us[tid + j * kBlock] = nx[j];
+            if (tid < pn * NC) rs[tid] = nr;
         };
         fetch(0);
         __syncthreads();
-#pragma unroll
-        for (int j = 0; j < PER; ++j) us[tid + j * kBlock] = nx[j];
+        put();
         fetch(1);
         __syncthreads();
         for (int c = 0; c < nchunks; ++c) {
             const int nn = min(NC, N - c * NC);
             if (live) {
-                const size_t cell0 = (size_t)p * f.ldp + (size_t)c * NC;
-#pragma unroll 8
+                const uint2* rp = rs + pl * NC;
+#pragma unroll 4
                 for (int n = 0; n < nn; ++n) {
-                    const float4 x = Cell<E>::ldg_plain(f.R, cell0 + n);
+                    const float4 x = bf_unpack(rp[n]);
                     const float2 uu = *reinterpret_cast<const float2*>(us + n * 64 + i0);
                     a0[0] = fmaf(x.x, uu.x, a0[0]);
                     a1[0] = fmaf(x.x, uu.y, a1[0]);
@@ -2006,15 +2015,14 @@ __device__ __forceinline__ void q_rows_from_residual(const FitArgs& f, SmemFit& 
                 }
             }
             __syncthreads();
-#pragma unroll
-            for (int j = 0; j < PER; ++j) us[tid + j * kBlock] = nx[j];
+            put();
             fetch(c + 2);
             __syncthreads();
         }
         if (live)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                float* row = Ql + (size_t)(4 * p + q) * f.ldv;
+                float* row = Ql + (size_t)(4 * (pa + pl) + q) * f.ldv;
                 row[i0] = a0[q];
                 if (i0 + 1 < k) row[i0 + 1] = a1[q];
             }
