@@ -238,7 +238,7 @@ def host_identity():
 
 
 def cpu_baseline(X64, w, algo, sample_comp):
-    """The FP64 oracle on the host cores (SURVEY's CPU-baseline plan): the -O2 and -O3
+    """The FP64 oracle on the host cores as the CPU baseline: the -O2 and -O3
     builds, single-threaded and with OpenMP on every core.  The multi-threaded builds fit
     the whole workload (every component, measured); the single-threaded ones time the
     first `sample_comp` components and their whole-fit time is the multi-threaded whole
