@@ -11,10 +11,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libgspca.so")
-SOURCES = ["gspca_api.cu", "noalloc_api.cu", "batch_api.cu", "warmstart_api.cu", "fit64_api.cu", "block_api.cu",
-           "fit_f32_a.cu", "fit_f32_b.cu", "fit_f32_c.cu", "fit_bf16_a.cu", "fit_bf16_b.cu", "fit_bf16_c.cu",
-           "fit_f32_w.cu", "fit_bf16_w.cu", "fit_f32_g.cu", "fit_bf16_g.cu",
-           "fit_f32_k.cu", "fit_bf16_k.cu"]
+SOURCES = ["gspca_api.cu", "noalloc_api.cu", "batch_api.cu", "warmstart_api.cu", "fit64_api.cu", "block_api.cu"] + [
+    f"fit_{t}_{u}.cu" for t in ("f32", "bf16") for u in ("a", "b", "c", "d", "g", "h", "k", "l", "w", "x")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,9 +1,7 @@
 // Kernels for storage type float for more than 128 components (the wide factor
-// products): the fit kernel for every column-block count.
+// products): the fit kernel for up to 2048 columns per CTA.
 #include "fit_inst.cuh"
 
 GSPCA_INSTANTIATE_FIT_WIDE(1, float)
 GSPCA_INSTANTIATE_FIT_WIDE(2, float)
 GSPCA_INSTANTIATE_FIT_WIDE(4, float)
-GSPCA_INSTANTIATE_FIT_WIDE(8, float)
-GSPCA_INSTANTIATE_FIT_WIDE(16, float)
