@@ -135,3 +135,12 @@ def test_binding_structs_match_the_header_layout(struct, pyname, rename):
     size, offs = _c_layout(struct, names)
     assert ctypes.sizeof(cls) == size
     assert [getattr(cls, n).offset for n, _ in cls._fields_] == offs
+
+
+def test_every_cuda_source_is_built():
+    """Every translation unit under csrc/ is in the build list (a unit left out would leave its
+    kernel instantiations undefined only at load time)."""
+    from paper_0811_1081_gb300 import buildlib as b
+
+    units = sorted(f for f in os.listdir(b.CSRC) if f.endswith(".cu"))
+    assert sorted(b.SOURCES) == units
